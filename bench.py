@@ -1,0 +1,374 @@
+#!/usr/bin/env python3
+"""Benchmark of the random-phase Trotter path on GB300.
+
+One bench step = one whole job of the hot path: random-phase initialization
+(Philox phases), `trotter_steps` second-order Trotter steps (FP64 gate/phase
+tables, tile sweeps with the diagonal phase and the fused P/norm reduction).
+The default workload is the 2x15 XY ladder (M = 30, 2^30 complex64
+amplitudes = 8 GiB, leg 1, rung 0.5, dt 0.05, 200 steps), the largest case,
+where the HBM roofline applies; the state (8 GiB) is far larger than L2, so
+no flush is needed between steps.
+
+  value   amp-gate updates/s = 2^M * 2B * trotter_steps / device time per job,
+          summed over replicas (N > 1 runs one independent job per GPU);
+  e2e     the same through the public API with host inputs and the P(t)
+          series copied back (system + state creation, init, evolve, read);
+  roofline  the tile-sweep kernel: algorithmic bytes (one read + one write of
+          the state) per launch / its mean launch time (CUDA events around every
+          launch on the state's stream) against the measured HBM copy peak;
+  fp64    the complex128 path on the same workload (fewer Trotter steps, rate);
+  cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload.
+
+`--impl reference` times the CPU oracle (there is no other implementation of
+the paper's method) on the same workload and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "amp·gate updates/s, HBM GB/s FP32 vs FP64; serve p50/p99 latency @|ΔP|≤1e-4"
+UNIT = "amp-gate updates/s"
+
+
+def _peaks():
+    try:
+        return json.loads((ROOT / "MEASURED_PEAKS.json").read_text()), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+def workload(name: str):
+    from paper_0710_3747_gb300 import workloads as W
+    if name == "ladder_m30":
+        return W.ladder_m30(), "c64", "ladder_2x15_M30_xy_dt0.05_200steps"
+    if name == "star_m20":
+        return W.star_m20(), "c64", "star_dipolar_M20_dt0.02_1000steps"
+    if name == "ladder_m14":
+        return W.ladder_m14(), "c64", "ladder_2x7_M14_xy_dt0.05_400steps"
+    if name == "ladder_m26":  # profiling case: 512 MiB state, larger than L2
+        job = W.ladder_m30()
+        job.J = W.ladder(13, 1.0, 0.5)
+        job.steps = 10
+        return job, "c64", "ladder_2x13_M26_xy_dt0.05_10steps"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def updates_per_job(M: int, nbonds: int, steps: int) -> float:
+    # 2B half-step bond gates per Trotter step, each touching the 2^M-amplitude state
+    return float(2 ** M) * 2 * nbonds * steps
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id is not None:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(job, gates: int, threads: int, repeats: int = 1, warmup: int = 0):
+    """Time `gates` flip-flop gate applications of the oracle (canonical order,
+    tau = dt/2) on the job's random-phase state at full size; the state's
+    initialization is set-up, outside the timing."""
+    import oracle
+    a, b = oracle.couplings(job.J, job.htype)
+    bonds = oracle.canonical_bonds(b)
+    psi = oracle.init_random_phase(job.M, job.seed, threads=threads)
+    times = []
+    for r in range(warmup + repeats):
+        t0 = time.perf_counter()
+        for k in range(gates):
+            i, j = bonds[k % len(bonds)]
+            oracle.flipflop(psi, i, j, b[i, j], 0.5 * job.dt, threads=threads)
+        dt = time.perf_counter() - t0
+        if r >= warmup:
+            times.append(dt)
+    del psi
+    return times
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return 0
+    job, prec, wname = workload(args.workload)
+    threads = os.cpu_count() or 1
+    gates = args.ref_gates
+    times = oracle_sample(job, gates, threads, repeats=args.steps, warmup=args.warmup)
+    per = statistics.mean(times)
+    value = gates * float(2 ** job.M) / per
+    sample = (f"FP64 CPU oracle, {gates} flip-flop gate applications of the M={job.M} "
+              f"{job.kind} state per step (2^{job.M} complex128 amplitudes), {threads} threads; "
+              f"state initialization untimed")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wname, "M": job.M, "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+
+    from paper_0710_3747_gb300 import spinrp
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    spinrp.lib()
+    job, prec, wname = workload(args.workload)
+    sysm = spinrp.System(job.J, job.htype)
+    nb = len(sysm.bonds())
+    info = sysm.plan_info(prec)
+    st = spinrp.State(sysm, prec, series_cap=job.steps + 1)
+    stream = torch.cuda.current_stream()
+
+    def one_job():
+        st.init_random_phase(job.seed + rank)
+        st.evolve(job.dt, job.steps)
+
+    for _ in range(args.warmup):
+        one_job()
+    torch.cuda.synchronize()
+
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(local_rank).uuid)
+        if not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        gpu_id = str(local_rank)
+
+    st.profile(True)
+    n0 = spinrp.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_id) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            one_job()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = spinrp.launch_count() - n0
+    st.profile(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    P32 = st.polarization()
+    sweep_ms, sweep_n = st.profile_read(spinrp.KERNEL_SWEEP)
+    init_ms, init_n = st.profile_read(spinrp.KERNEL_INIT)
+    upd = updates_per_job(job.M, nb, job.steps)
+    value = world * upd / (ms / 1e3)
+
+    # roofline of the tile-sweep kernel
+    peaks, peak_src = _peaks()
+    amp_bytes = 8 if prec == "c64" else 16
+    bytes_per_launch = 2 * amp_bytes * 2 ** job.M
+    sweep_avg_s = sweep_ms / max(sweep_n, 1) / 1e3
+    achieved = bytes_per_launch / sweep_avg_s / 1e9
+    traffic = None
+    tfile = ROOT / "profiles" / f"traffic_{args.workload}_{prec}.json"
+    if tfile.exists():
+        try:
+            tinfo = json.loads(tfile.read_text())
+            import hashlib
+            h = hashlib.sha256((ROOT / "paper_0710_3747_gb300" / "csrc" / "kernels.cuh").read_bytes()).hexdigest()
+            if tinfo.get("kernels_sha256") == h:
+                traffic = tinfo.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "kernel": "sweep_kernel<float>" if prec == "c64" else "sweep_kernel<double>",
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+                "launches": sweep_n, "mean_launch_ms": sweep_avg_s * 1e3,
+                "sweep_share_of_job": sweep_ms / (ms * args.steps)}
+    # whole-step roofline: minimal sweeps (2 per step) at the measured peak
+    min_bytes_step = 2 * bytes_per_launch
+    step_roof = {"min_sweeps_per_step": 2, "sweeps_per_step": info["sweeps_per_step"],
+                 "frac_of_measured_peak": (min_bytes_step * job.steps / (ms / 1e3) / 1e9) / peaks["hbm_gbs"],
+                 "frac_of_8TBps": (min_bytes_step * job.steps / (ms / 1e3) / 1e9) / 8000.0}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == "c64" else "f64", "data": "synthetic",
+        "config": {"workload": wname, "M": job.M, "bonds": nb, "trotter_steps": job.steps,
+                   "dt": job.dt, "amplitudes": "complex64" if prec == "c64" else "complex128",
+                   "tile_K": info["K"], "sweeps_per_step": info["sweeps_per_step"],
+                   "state_bytes": amp_bytes * 2 ** job.M,
+                   "l2": "inputs larger than L2 (state >> 129 MB), no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline, "hbm_step_roofline": step_roof, "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+
+    # end to end through the public API: host J in, P(t) series out
+    if not args.skip_e2e:
+        def e2e_job():
+            s2 = spinrp.System(job.J, job.htype)
+            st2 = spinrp.State(s2, prec, series_cap=job.steps + 1)
+            st2.init_random_phase(job.seed + rank).evolve(job.dt, job.steps)
+            P = st2.polarization()
+            N = st2.norm_series()
+            h2d, d2h = st2.transfer_bytes()
+            st2.close()
+            return P, N, h2d + job.J.nbytes, d2h
+        e2e_job()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _, _, h2d, d2h = e2e_job()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        out["e2e"] = {"value": world * upd / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h), "s_per_step": e2e_s}
+
+    # the FP64 (complex128) path on the same workload
+    if not args.skip_fp64 and args.fp64_steps > 0:
+        st64 = spinrp.State(sysm, "c128", series_cap=args.fp64_steps + 1)
+        st64.init_random_phase(job.seed + rank).evolve(job.dt, 1)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st64.init_random_phase(job.seed + rank)
+        f0.record(stream)
+        st64.evolve(job.dt, args.fp64_steps)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        P64 = st64.polarization()
+        n = min(len(P64), len(P32))
+        out["fp64"] = {"value": world * updates_per_job(job.M, nb, args.fp64_steps) / (ms64 / 1e3),
+                       "unit": UNIT, "trotter_steps": args.fp64_steps, "ms": ms64,
+                       "fp32_vs_fp64_max_dP": float(np.max(np.abs(P32[:n] - P64[:n])))}
+        st64.close()
+
+    if rank == 0 and not args.skip_cpu:
+        threads = os.cpu_count() or 1
+        gates = args.cpu_gates
+        t = oracle_sample(job, gates, threads, repeats=1)[0]
+        out["cpu_baseline"] = {
+            "value": gates * float(2 ** job.M) / t, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"FP64 CPU oracle, {gates} flip-flop gate applications (canonical order) of the "
+                       f"M={job.M} state, {threads} threads, {t:.1f} s; initialization untimed"),
+        }
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="ladder_m30", choices=["ladder_m30", "star_m20", "ladder_m14", "ladder_m26"])
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--cpu-gates", type=int, default=43)
+    ap.add_argument("--ref-gates", type=int, default=16)
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,232 @@
+/*
+ * spinrp.h -- C ABI of the GB300 random-phase spin-dynamics library.
+ *
+ * The library evolves ONE pure state of M spins-1/2 (2^M amplitudes, resident
+ * on the GPU) with the method of Alvarez, Danieli, Levstein & Pastawski,
+ * "Quantum parallelism as a tool for ensemble spin dynamics calculations"
+ * (arXiv:0710.3747):
+ *
+ *   - the state is the entangled random-phase state of the paper's "Testing the
+ *     quantum parallelism" section, spin 1 up and every Zeeman basis state |r>
+ *     of spins 2..M with weight 2^{-(M-1)/2} and an independent phase, which
+ *     stands for the infinite-temperature ensemble of Eq. 1 (p_i = 1/2^{M-1});
+ *   - the Hamiltonian is the secular spin-spin Hamiltonian of the "Spin systems
+ *     with different coupling networks" section,
+ *        H = sum_{i<j} [ a_ij S^z_i S^z_j + 1/2 b_ij (S^+_i S^-_j + S^-_i S^+_j) ];
+ *   - the evolution is the symmetric second-order Trotter-Suzuki product the
+ *     paper names (introduction, summary), with the splitting
+ *        U(dt) = e^{-i dt/2 D} F_1 .. F_B F_B .. F_1 e^{-i dt/2 D},
+ *     D = sum a_ij S^z_i S^z_j and F_k = exp(-i dt/2 b_k (S^x S^x + S^y S^y))
+ *     on flip-flop bond k, bonds in canonical order (all pairs i<j with
+ *     b_ij != 0, lexicographic);
+ *   - after every step the library records the local polarization
+ *     P_11(t) = 2 [W_11(t) - 1/2] of Eq. 2 with m = m' = 1 (computed as
+ *     (N_up - N_dn)/(N_up + N_dn) of spin 1) and the norm, in FP64.
+ *
+ * Conventions: spins are numbered 1..M in the API; coupling matrices are M x M
+ * row-major FP64, symmetric, zero diagonal; hbar = 1.  Amplitudes exchanged
+ * with the host are in LOGICAL order (bit n-1 of the index = spin n, set = up)
+ * as interleaved (re, im) FP64 pairs; on the device the library may store
+ * them with its own bit permutation.
+ *
+ * Errors: every call returns SPINRP_OK (0) or a positive SPINRP_E* code and
+ * never aborts; spinrp_last_error() gives a message for the calling thread.
+ * Ownership: the caller owns the handles it creates and destroys them; the
+ * library never frees caller memory.  Device work is asynchronous on the
+ * stream given at state creation, except where a call says it synchronizes.
+ * Handles are not thread-safe: one thread at a time per handle.
+ */
+#ifndef SPINRP_H
+#define SPINRP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPINRP_OK 0
+#define SPINRP_EINVAL 1       /* bad argument (size, index, type, capacity) */
+#define SPINRP_ENOMEM 2       /* host or device allocation failed */
+#define SPINRP_ECUDA 3        /* a CUDA runtime call or kernel launch failed */
+#define SPINRP_ETIMEOUT 4     /* a bounded device-side wait gave up */
+#define SPINRP_EUNSUPPORTED 5 /* valid request this build does not implement */
+#define SPINRP_ESTATE 6       /* call out of order (e.g. evolve before init) */
+
+/* Hamiltonian families of the paper ("Spin systems with different coupling
+ * networks"): b/a = 0 Ising, a/b = 0 XY, a/b = 1 isotropic, a/b = -2 secular
+ * dipolar truncated by a field along z.  For a coupling matrix J:
+ *   XY:        a = 0,   b = J          (H = sum J (SxSx + SySy))
+ *   DIPOLAR:   a = 2J,  b = -J         (H = sum J [2 SzSz - (SxSx + SySy)])
+ *   ISOTROPIC: a = J,   b = J
+ *   ISING:     a = J,   b = 0
+ *   GENERIC:   a = a_generic, b = J                                         */
+#define SPINRP_XY 0
+#define SPINRP_DIPOLAR 1
+#define SPINRP_ISOTROPIC 2
+#define SPINRP_ISING 3
+#define SPINRP_GENERIC 4
+
+/* Amplitude precision on the device: complex64 (FP32 gate arithmetic) or
+ * complex128 (FP64).  Gate coefficients, diagonal phases' integer tables and
+ * all reductions are generated / accumulated in FP64 in both cases. */
+#define SPINRP_C64 0
+#define SPINRP_C128 1
+
+typedef struct spinrp_system spinrp_system; /* host-side spin system (couplings, plan) */
+typedef struct spinrp_state spinrp_state;   /* one device-resident state + P(t) series */
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *spinrp_last_error(void);
+
+/* Library version string. */
+const char *spinrp_version(void);
+
+/* ---- spin systems (host only, no GPU needed) ---------------------------- */
+
+/* Create a spin system of M spins (2 <= M <= 34) from the coupling matrix J
+ * (M*M doubles, row-major) and Hamiltonian family htype (SPINRP_XY ..
+ * SPINRP_GENERIC); a_generic is read only for SPINRP_GENERIC (else may be
+ * NULL).  Only the upper triangle i<j is read.  The system copies its inputs.
+ * The paper's problem statement: H of "Spin systems with different coupling
+ * networks".  On success *out receives a handle to free with
+ * spinrp_system_destroy.  Errors: SPINRP_EINVAL (M, htype, NULL, non-finite
+ * coupling), SPINRP_ENOMEM. */
+int spinrp_system_create(int M, const double *J, int htype, const double *a_generic,
+                         spinrp_system **out);
+
+/* Free a system (NULL is ignored).  States created from it stay valid. */
+void spinrp_system_destroy(spinrp_system *sys);
+
+/* Number of spins. */
+int spinrp_system_num_spins(const spinrp_system *sys);
+
+/* Flip-flop bonds in the canonical order of the forward half step: pairs
+ * (i, j), 1-based, i < j, b_ij != 0, lexicographic.  Writes min(n, cap)
+ * pairs (2 ints each) to pairs (may be NULL when cap = 0) and the total count
+ * to *n.  Errors: SPINRP_EINVAL. */
+int spinrp_system_bonds(const spinrp_system *sys, int32_t *pairs, int cap, int *n);
+
+/* Choose the shared-memory tile width K (number of spins a tile spans, 2^K
+ * amplitudes per tile) used for precision prec by states created afterwards;
+ * K = 0 restores the built-in default.  Valid K: 1..14 for SPINRP_C64,
+ * 1..13 for SPINRP_C128 (clipped to M).  This is the autotuner's knob.
+ * Errors: SPINRP_EINVAL. */
+int spinrp_system_set_tile(spinrp_system *sys, int prec, int K);
+
+/* Describe the sweep plan the library would use for precision prec: number
+ * of segments the forward half step is cut into (*segments), device sweeps
+ * per Trotter step in the steady state (*sweeps_per_step) and the tile width
+ * (*K).  Any output pointer may be NULL.  Host only. */
+int spinrp_system_plan_info(const spinrp_system *sys, int prec, int *segments,
+                            int *sweeps_per_step, int *K);
+
+/* Export the plan: the flip-flop gates of one forward half step in the order
+ * the device applies them, as 1-based pairs (2 ints each), with the index of
+ * the segment (sweep tile) each one runs in.  Writes min(n, cap) entries and
+ * the total to *n.  For checking that the device order is the canonical one
+ * up to exchanges of gates on disjoint spins. */
+int spinrp_system_plan_gates(const spinrp_system *sys, int prec, int32_t *pairs,
+                             int32_t *segment, int cap, int *n);
+
+/* ---- states ----------------------------------------------------------- */
+
+/* Device memory a state of system sys at precision prec needs: *psi_bytes
+ * for the 2^M amplitudes and *work_bytes for everything else (FP64 P/norm
+ * series of series_cap entries, reduction partials, gate tables, plan). */
+int spinrp_state_bytes(const spinrp_system *sys, int prec, int64_t series_cap,
+                       size_t *psi_bytes, size_t *work_bytes);
+
+/* Create a state on the current CUDA device.  stream is a cudaStream_t (NULL
+ * = default stream).  series_cap is the number of P(t) entries the state can
+ * record (init records one, each Trotter step one).  psi and work are device
+ * buffers of at least the sizes spinrp_state_bytes reports, 256-byte aligned,
+ * owned by the caller and kept alive until spinrp_state_destroy; either may be
+ * NULL, and the library then allocates (and later frees) that buffer itself
+ * with cudaMalloc.  The state copies what it needs from sys.
+ * Errors: SPINRP_EINVAL, SPINRP_ENOMEM, SPINRP_ECUDA. */
+int spinrp_state_create(const spinrp_system *sys, int prec, void *stream, int64_t series_cap,
+                        void *psi, void *work, spinrp_state **out);
+
+/* Free a state and any memory the library allocated for it (NULL ignored).
+ * Synchronizes the state's stream first. */
+void spinrp_state_destroy(spinrp_state *st);
+
+/* Set the state to the paper's entangled random-phase state
+ *   |Psi> = 2^{-(M-1)/2} sum_r e^{i phi_r} |up>_1 (x) |r>,
+ * phi_r = 2 pi u, u = top 53 bits of the first two output words of
+ * Philox4x32-10(counter = (lo32 r, hi32 r, 0, 0), key = (lo32 seed, hi32 seed))
+ * times 2^-53, r = the basis index of spins 2..M (spin n at bit n-2).  Resets
+ * the series and records P(0).  Asynchronous. */
+int spinrp_state_init_random_phase(spinrp_state *st, uint64_t seed);
+
+/* Load an arbitrary state from the host: 2^M complex amplitudes in logical
+ * order as interleaved FP64 (re, im).  Resets the series and records P(0).
+ * Synchronizes. */
+int spinrp_state_load(spinrp_state *st, const double *amps);
+
+/* Evolve by `steps` second-order Trotter steps of size dt (order must be 2;
+ * dt may be negative), appending P and the norm after every step to the
+ * series.  Asynchronous on the state's stream.  Errors: SPINRP_ESTATE before
+ * init/load, SPINRP_EINVAL if the series would exceed its capacity or dt is
+ * not finite, SPINRP_EUNSUPPORTED for order != 2, SPINRP_ECUDA. */
+int spinrp_evolve(spinrp_state *st, double dt, int64_t steps, int order);
+
+/* Number of entries recorded so far (1 after init, +1 per step). */
+int64_t spinrp_series_length(const spinrp_state *st);
+
+/* Copy the recorded polarization series P_{site,1}(t_k), k = 0..len-1, to
+ * the host buffer out (min(len, cap) doubles); *n receives len.  Only site 1
+ * (the initially polarized spin) is recorded by this build; other sites give
+ * SPINRP_EUNSUPPORTED.  Synchronizes the state's stream. */
+int spinrp_polarization(spinrp_state *st, int site, double *out, int64_t cap, int64_t *n);
+
+/* Same for the norm sum_x |psi_x|^2 after each step. */
+int spinrp_norm_series(spinrp_state *st, double *out, int64_t cap, int64_t *n);
+
+/* Read n amplitudes with LOGICAL basis indices idx[k] (0 <= idx < 2^M) into
+ * out (2n doubles, re/im).  Synchronizes. */
+int spinrp_state_read(spinrp_state *st, const int64_t *idx, int64_t n, double *out);
+
+/* Device pointer of the amplitude buffer and the device-side bit layout:
+ * layout[q] receives the physical bit position of spin q+1 (M ints).  The
+ * layout is the same after every complete spinrp_evolve call. */
+int spinrp_state_layout(const spinrp_state *st, int32_t *layout, void **psi);
+
+/* ---- measurement (no counterpart in the paper) ------------------------- */
+
+/* Kernel kinds for spinrp_profile_read. */
+#define SPINRP_KERNEL_SWEEP 0  /* tile sweeps (gates, diagonal phase, reduction) */
+#define SPINRP_KERNEL_INIT 1   /* random-phase initialization */
+#define SPINRP_KERNEL_TABLES 2 /* FP64 gate / phase table generation */
+
+/* enable != 0: from now on bracket every kernel this state launches with a
+ * pair of CUDA events on the state's stream (clearing earlier records);
+ * enable == 0: stop recording (records are kept for spinrp_profile_read). */
+int spinrp_profile(spinrp_state *st, int enable);
+
+/* Total device time (ms) and number of launches recorded for one kernel
+ * kind.  Synchronizes the state's stream. */
+int spinrp_profile_read(spinrp_state *st, int kind, double *total_ms, int64_t *launches);
+
+/* Number of kernels the library has launched in this process (all states). */
+int64_t spinrp_launch_count(void);
+
+/* Bytes this state has copied host->device and device->host so far. */
+int spinrp_state_transfer_bytes(const spinrp_state *st, int64_t *h2d, int64_t *d2h);
+
+/* Host self-check of the device program for precision prec (no GPU): every
+ * sweep's register-blocked phase program is executed on a random host tile
+ * and compared with the sweep's plain op list, and the element-wise ops are
+ * checked to stay in order.  Also reports the mean number of phases per sweep
+ * and of gates per phase (either pointer may be NULL).  SPINRP_OK when every
+ * sweep agrees, SPINRP_EINVAL with a message otherwise. */
+int spinrp_system_plan_check(const spinrp_system *sys, int prec, double *phases_per_sweep,
+                             double *gates_per_phase);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPINRP_H */

@@ -1,0 +1,1015 @@
+// api.cu -- C ABI (include/spinrp.h): spin systems, the sweep plan, device
+// states and the evolve loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/spinrp.h"
+#include "internal.h"
+#include "kernels.cuh"
+
+using namespace spinrp;
+
+// ---------------------------------------------------------------------------
+// error reporting
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(call)                                                                 \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) return fail(SPINRP_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static std::atomic<int64_t> g_launches{0};
+
+extern "C" const char *spinrp_last_error(void) { return g_err.c_str(); }
+extern "C" int64_t spinrp_launch_count(void) { return g_launches.load(); }
+extern "C" const char *spinrp_version(void) { return "spinrp 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// systems
+// ---------------------------------------------------------------------------
+struct spinrp_system {
+  int M = 0, htype = 0;
+  std::vector<double> a, b;  // M*M, symmetric, zero diagonal
+  std::vector<std::pair<int, int>> bonds;
+  int tileK[2] = {0, 0};
+};
+
+static bool any_diag(const spinrp_system &s) {
+  for (int i = 0; i < s.M; ++i)
+    for (int j = i + 1; j < s.M; ++j)
+      if (s.a[i * s.M + j] != 0.0) return true;
+  return false;
+}
+
+extern "C" int spinrp_system_create(int M, const double *J, int htype, const double *a_generic,
+                                    spinrp_system **out) {
+  if (!out) return fail(SPINRP_EINVAL, "system_create: out is NULL");
+  *out = nullptr;
+  if (M < 2 || M > kMaxM) return fail(SPINRP_EINVAL, "system_create: M=%d outside 2..%d", M, kMaxM);
+  if (!J) return fail(SPINRP_EINVAL, "system_create: J is NULL");
+  if (htype < SPINRP_XY || htype > SPINRP_GENERIC)
+    return fail(SPINRP_EINVAL, "system_create: unknown Hamiltonian type %d", htype);
+  if (htype == SPINRP_GENERIC && !a_generic)
+    return fail(SPINRP_EINVAL, "system_create: GENERIC needs a_generic");
+  spinrp_system *s = new (std::nothrow) spinrp_system;
+  if (!s) return fail(SPINRP_ENOMEM, "system_create: out of host memory");
+  s->M = M;
+  s->htype = htype;
+  s->a.assign(M * M, 0.0);
+  s->b.assign(M * M, 0.0);
+  for (int i = 0; i < M; ++i)
+    for (int j = i + 1; j < M; ++j) {
+      const double Jij = J[i * M + j];
+      const double ag = a_generic ? a_generic[i * M + j] : 0.0;
+      if (!std::isfinite(Jij) || !std::isfinite(ag)) {
+        delete s;
+        return fail(SPINRP_EINVAL, "system_create: non-finite coupling at (%d,%d)", i + 1, j + 1);
+      }
+      double aij = 0.0, bij = 0.0;
+      switch (htype) {
+        case SPINRP_XY: bij = Jij; break;
+        case SPINRP_DIPOLAR: aij = 2.0 * Jij, bij = -Jij; break;
+        case SPINRP_ISOTROPIC: aij = Jij, bij = Jij; break;
+        case SPINRP_ISING: aij = Jij; break;
+        default: aij = ag, bij = Jij; break;
+      }
+      s->a[i * M + j] = s->a[j * M + i] = aij;
+      s->b[i * M + j] = s->b[j * M + i] = bij;
+    }
+  for (int i = 0; i < M; ++i)
+    for (int j = i + 1; j < M; ++j)
+      if (s->b[i * M + j] != 0.0) s->bonds.push_back({i, j});
+  *out = s;
+  return SPINRP_OK;
+}
+
+extern "C" void spinrp_system_destroy(spinrp_system *sys) { delete sys; }
+
+extern "C" int spinrp_system_num_spins(const spinrp_system *sys) { return sys ? sys->M : 0; }
+
+extern "C" int spinrp_system_bonds(const spinrp_system *sys, int32_t *pairs, int cap, int *n) {
+  if (!sys || !n || (cap > 0 && !pairs)) return fail(SPINRP_EINVAL, "system_bonds: bad argument");
+  *n = (int)sys->bonds.size();
+  for (int k = 0; k < std::min(cap, *n); ++k) {
+    pairs[2 * k] = sys->bonds[k].first + 1;
+    pairs[2 * k + 1] = sys->bonds[k].second + 1;
+  }
+  return SPINRP_OK;
+}
+
+static int default_K(int prec) { return prec == SPINRP_C64 ? 14 : 13; }
+static int low_bits(int prec) { return prec == SPINRP_C64 ? 4 : 3; }  // 128-byte runs
+
+extern "C" int spinrp_system_set_tile(spinrp_system *sys, int prec, int K) {
+  if (!sys || (prec != SPINRP_C64 && prec != SPINRP_C128))
+    return fail(SPINRP_EINVAL, "system_set_tile: bad argument");
+  const int kmax = prec == SPINRP_C64 ? 14 : 13;
+  if (K < 0 || K > kmax) return fail(SPINRP_EINVAL, "system_set_tile: K=%d outside 0..%d", K, kmax);
+  sys->tileK[prec] = K;
+  return SPINRP_OK;
+}
+
+static int make_plan(const spinrp_system &s, int prec, Plan *plan) {
+  int K = s.tileK[prec] ? s.tileK[prec] : default_K(prec);
+  K = std::min(K, s.M);
+  std::string err;
+  if (!build_plan(s.M, s.bonds, K, low_bits(prec), plan, &err))
+    return fail(SPINRP_EINVAL, "%s", err.c_str());
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_system_plan_info(const spinrp_system *sys, int prec, int *segments,
+                                       int *sweeps_per_step, int *K) {
+  if (!sys || (prec != SPINRP_C64 && prec != SPINRP_C128))
+    return fail(SPINRP_EINVAL, "system_plan_info: bad argument");
+  Plan p;
+  int rc = make_plan(*sys, prec, &p);
+  if (rc) return rc;
+  if (segments) *segments = p.segments();
+  if (sweeps_per_step) *sweeps_per_step = p.sweeps_per_step();
+  if (K) *K = p.K;
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_system_plan_gates(const spinrp_system *sys, int prec, int32_t *pairs,
+                                        int32_t *segment, int cap, int *n) {
+  if (!sys || !n || (prec != SPINRP_C64 && prec != SPINRP_C128) || (cap > 0 && (!pairs || !segment)))
+    return fail(SPINRP_EINVAL, "system_plan_gates: bad argument");
+  Plan p;
+  int rc = make_plan(*sys, prec, &p);
+  if (rc) return rc;
+  int k = 0;
+  for (int sgi = 0; sgi < p.segments(); ++sgi)
+    for (const PlanGate &g : p.seg[sgi]) {
+      if (k < cap) pairs[2 * k] = g.i + 1, pairs[2 * k + 1] = g.j + 1, segment[k] = sgi;
+      ++k;
+    }
+  *n = k;
+  return SPINRP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// states
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kStage = 1 << 16;  // amplitudes per host<->device staging chunk
+
+struct PassSet {
+  // sweep descriptors (host copies) and their op lists
+  std::vector<PassDesc> desc;
+  std::vector<Op> ops;
+  // register-blocked programs (complex64 path)
+  std::vector<PhaseDesc> phases;
+  std::vector<ROp> rops;
+  // launch roles (indices into desc)
+  int head = -1, mid = -1, join = -1, tail = -1;
+  std::vector<int> body, bodyr;
+  int only = -1, first = -1, midstep = -1, last = -1;
+};
+
+struct Layout {  // byte offsets inside the work buffer
+  size_t series, partials, ticket, coefs, bvals, adiag, qdiag, passes, ops, phases, rops, stage,
+      stage_idx, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct spinrp_state {
+  int M = 0, prec = 0, device = 0;
+  cudaStream_t stream = nullptr;
+  void *psi = nullptr;
+  unsigned char *work = nullptr;
+  bool own_psi = false, own_work = false;
+  int64_t cap = 0, len = 0;
+  bool ready = false;
+  bool has_diag = false;
+  int nb = 0;
+  Plan plan;
+  PassSet ps;
+  Layout lay{};
+  int max_blocks = 0;
+  double coef_dt = NAN;
+  std::vector<double> bvals, a;
+  std::vector<uint8_t> logical_of;  // physical position -> logical spin
+  // device views
+  double *series = nullptr;
+  double2 *partials = nullptr;
+  unsigned *ticket = nullptr;
+  GateCoef *coefs = nullptr;
+  double *d_bvals = nullptr, *d_a = nullptr;
+  uint64_t *qdiag = nullptr;
+  PassDesc *passes = nullptr;
+  Op *ops = nullptr;
+  PhaseDesc *phases = nullptr;
+  ROp *rops = nullptr;
+  bool v2 = false;
+  double2 *stage = nullptr;
+  int64_t *stage_idx = nullptr;
+  // measurement
+  bool prof = false;
+  std::vector<cudaEvent_t> ev[3];  // start/stop pairs per kernel kind
+  int64_t h2d = 0, d2h = 0;
+};
+
+// Bracket a launch of kernel kind `kind` with events when profiling is on.
+static void prof_mark(spinrp_state *st, int kind) {
+  if (!st->prof) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) == cudaSuccess) {
+    cudaEventRecord(e, st->stream);
+    st->ev[kind].push_back(e);
+  }
+}
+
+static void prof_clear(spinrp_state *st) {
+  for (auto &v : st->ev) {
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
+    v.clear();
+  }
+}
+
+static int init_blocks(int M) {
+  const int64_t n = (int64_t(1) << M) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(n, 152 * 8));
+}
+
+// Build the sweep descriptors for plan p.
+static void build_passes(const Plan &p, bool has_diag, PassSet *ps) {
+  const int M = p.M, K = p.K, c = p.c;
+  ps->desc.clear();
+  ps->ops.clear();
+  std::vector<std::vector<int>> pass_in;  // read layout (logical -> physical) of each pass
+  // A pass over segment seg that reads the state in layout Lin and writes it in
+  // layout Lout (Lout permutes the tile's spins among the tile's positions).
+  auto new_pass = [&](int seg, const std::vector<int> &Lin, const std::vector<int> &Lout) -> int {
+    PassDesc d;
+    memset(&d, 0, sizeof d);
+    d.K = K;
+    std::vector<int> tpos;
+    for (int q : p.segQ[seg]) tpos.push_back(Lin[q]);
+    std::sort(tpos.begin(), tpos.end());
+    std::vector<char> in(M, 0);
+    for (int x : tpos) in[x] = 1;
+    int no = 0;
+    for (int x = 0; x < M; ++x)
+      if (!in[x]) d.outer_pos[no++] = (uint8_t)x;
+    std::vector<int> in_spin(M, -1), out_spin(M, -1);  // physical position -> spin
+    for (int q = 0; q < M; ++q) in_spin[Lin[q]] = q, out_spin[Lout[q]] = q;
+    d.relabel = 0;
+    for (int qo = 0; qo < K; ++qo) {
+      d.tile_pos[qo] = (uint8_t)tpos[qo];
+      const int spin = out_spin[tpos[qo]];
+      int qi = 0;
+      while (tpos[qi] != Lin[spin]) ++qi;
+      d.perm[qo] = (uint8_t)qi;
+      if (qi != qo) d.relabel = 1;
+    }
+    d.site_pos = Lin[0];
+    d.site_tile = -1;
+    for (int q = 0; q < K; ++q)
+      if (tpos[q] == Lin[0]) d.site_tile = q;
+    d.op0 = (int)ps->ops.size();
+    d.nops = 0;
+    ps->desc.push_back(d);
+    pass_in.push_back(Lin);
+    return (int)ps->desc.size() - 1;
+  };
+  auto tile_bit = [&](int pass, int logical) -> int {
+    const PassDesc &d = ps->desc[pass];
+    for (int q = 0; q < K; ++q)
+      if (d.tile_pos[q] == pass_in[pass][logical]) return q;
+    return -1;
+  };
+  auto push = [&](int pass, Op op) {
+    ps->ops.push_back(op);
+    ps->desc[pass].nops++;
+  };
+  auto gate = [&](int pass, const PlanGate &g, int variant) {
+    Op op{};
+    op.kind = OP_GATE;
+    op.u = (uint8_t)tile_bit(pass, g.i);
+    op.v = (uint8_t)tile_bit(pass, g.j);
+    op.coef = 2 * g.bond + variant;
+    push(pass, op);
+  };
+  auto diag = [&](int pass, int variant) {
+    if (!has_diag) return;
+    Op op{};
+    op.kind = OP_DIAG;
+    op.arg = (uint8_t)variant;
+    push(pass, op);
+  };
+  auto reduce = [&](int pass) {
+    Op op{};
+    op.kind = OP_REDUCE;
+    push(pass, op);
+    ps->desc[pass].has_reduce = 1;
+  };
+  auto fwd = [&](int pass, int seg) {
+    for (const PlanGate &g : p.seg[seg]) gate(pass, g, 0);
+  };
+  auto rev = [&](int pass, int seg) {
+    for (auto it = p.seg[seg].rbegin(); it != p.seg[seg].rend(); ++it) gate(pass, *it, 0);
+  };
+  // forward then reverse of one segment, the two middle copies of its last gate merged
+  auto fwd_rev = [&](int pass, int seg) {
+    const auto &g = p.seg[seg];
+    const int n = (int)g.size();
+    for (int k = 0; k + 1 < n; ++k) gate(pass, g[k], 0);
+    if (n > 0) gate(pass, g[n - 1], 1);
+    for (int k = n - 2; k >= 0; --k) gate(pass, g[k], 0);
+  };
+  const std::vector<int> &L0 = p.pos;
+  const int s = p.segments();
+  if (s == 1) {
+    // a whole Trotter step per sweep
+    ps->only = new_pass(0, L0, L0), diag(ps->only, 0), fwd_rev(ps->only, 0), reduce(ps->only), diag(ps->only, 0);
+    ps->first = new_pass(0, L0, L0), diag(ps->first, 0), fwd_rev(ps->first, 0), reduce(ps->first), diag(ps->first, 1);
+    ps->midstep = new_pass(0, L0, L0), fwd_rev(ps->midstep, 0), reduce(ps->midstep), diag(ps->midstep, 1);
+    ps->last = new_pass(0, L0, L0), fwd_rev(ps->last, 0), reduce(ps->last), diag(ps->last, 0);
+    return;
+  }
+  ps->head = new_pass(0, L0, L0), diag(ps->head, 0), fwd(ps->head, 0);
+  // ascending body sweeps: segment k reads layout L[k-1], writes L[k] with
+  // exit set X_k moved into the low bits
+  std::vector<std::vector<int>> L(s);
+  L[0] = L0;
+  for (int k = 1; k < s - 1; ++k) {
+    std::vector<int> out = L[k - 1];
+    std::vector<int> spin_at(M);
+    for (int q = 0; q < M; ++q) spin_at[out[q]] = q;
+    const std::vector<int> &X = p.exitX[k];
+    for (int x : X) {
+      if (out[x] < c) continue;
+      for (int pl = 0; pl < c; ++pl) {
+        const int y = spin_at[pl];
+        if (std::find(X.begin(), X.end(), y) != X.end()) continue;
+        std::swap(out[x], out[y]);
+        spin_at[out[x]] = x, spin_at[out[y]] = y;
+        break;
+      }
+    }
+    L[k] = out;
+    const int id = new_pass(k, L[k - 1], L[k]);
+    fwd(id, k);
+    ps->body.push_back(id);
+  }
+  ps->mid = new_pass(s - 1, L[s - 2], L[s - 2]), fwd_rev(ps->mid, s - 1);
+  for (int k = s - 2; k >= 1; --k) {
+    const int id = new_pass(k, L[k], L[k - 1]);
+    rev(id, k);
+    ps->bodyr.push_back(id);
+  }
+  ps->join = new_pass(0, L0, L0), rev(ps->join, 0), reduce(ps->join), diag(ps->join, 1), fwd(ps->join, 0);
+  ps->tail = new_pass(0, L0, L0), rev(ps->tail, 0), reduce(ps->tail), diag(ps->tail, 0);
+}
+
+static Layout work_layout(int M, int nb, int64_t cap, const PassSet &ps, int max_blocks) {
+  const size_t npass = ps.desc.size(), nops = ps.ops.size();
+  Layout L{};
+  size_t o = 0;
+  L.series = o, o = align256(o + sizeof(double) * 2 * std::max<int64_t>(cap, 1));
+  L.partials = o, o = align256(o + sizeof(double2) * max_blocks);
+  L.ticket = o, o = align256(o + 256);
+  L.coefs = o, o = align256(o + sizeof(GateCoef) * 2 * std::max(nb, 1));
+  L.bvals = o, o = align256(o + sizeof(double) * std::max(nb, 1));
+  L.adiag = o, o = align256(o + sizeof(double) * M * M);
+  L.qdiag = o, o = align256(o + sizeof(uint64_t) * 2 * M * M);
+  L.passes = o, o = align256(o + sizeof(PassDesc) * std::max<size_t>(npass, 1));
+  L.ops = o, o = align256(o + sizeof(Op) * std::max<size_t>(nops, 1));
+  L.phases = o, o = align256(o + sizeof(PhaseDesc) * std::max<size_t>(ps.phases.size(), 1));
+  L.rops = o, o = align256(o + sizeof(ROp) * std::max<size_t>(ps.rops.size(), 1));
+  L.stage = o, o = align256(o + sizeof(double2) * kStage);
+  L.stage_idx = o, o = align256(o + sizeof(int64_t) * kStage);
+  L.total = o;
+  return L;
+}
+
+// Register-blocked tiles are used for complex64 with K >= 10 (2^(K-5) threads).
+static bool use_phases(int prec, int K) { return prec == SPINRP_C64 && K >= 10; }
+
+// Compile every pass into phases of five register bits: the pass's gates
+// between two element-wise ops (diagonal phase, reduction) are cut into
+// phases by the same greedy as the sweep planner (gates on disjoint bits may
+// be exchanged, nothing else), and each element-wise op runs in the phase
+// after the gates it follows.
+static bool compile_phases(PassSet *ps, int K, std::string *err) {
+  ps->phases.clear();
+  ps->rops.clear();
+  for (PassDesc &d : ps->desc) {
+    d.phase0 = (int)ps->phases.size();
+    d.nphases = 0;
+    std::vector<ROp> pending;  // element-wise ops waiting for the next phase
+    auto new_phase = [&](const std::vector<int> &rb) {
+      PhaseDesc ph;
+      memset(&ph, 0, sizeof ph);
+      uint32_t isreg = 0;
+      for (int k = 0; k < kRegBits; ++k) ph.rb[k] = (uint8_t)rb[k], isreg |= 1u << rb[k];
+      // lane bits: four non-register bits of distinct residues mod 4 (bank-
+      // conflict free with the shared-memory swizzle), then the lowest left
+      std::vector<int> free_bits, lanes;
+      for (int b = 0; b < K; ++b)
+        if (!((isreg >> b) & 1)) free_bits.push_back(b);
+      uint32_t used = 0, res = 0;
+      for (int b : free_bits)
+        if (lanes.size() < 4 && !((res >> (b & 3)) & 1)) lanes.push_back(b), used |= 1u << b, res |= 1u << (b & 3);
+      for (int b : free_bits)
+        if (lanes.size() < 5 && !((used >> b) & 1)) lanes.push_back(b), used |= 1u << b;
+      for (int k = 0; k < 5; ++k) ph.lanes[k] = (uint8_t)lanes[k];
+      int nw = 0;
+      for (int b : free_bits)
+        if (!((used >> b) & 1)) ph.warps[nw++] = (uint8_t)b;
+      ph.op0 = (int)ps->rops.size();
+      ph.nops = 0;
+      for (const ROp &r : pending) ps->rops.push_back(r), ph.nops++;
+      pending.clear();
+      ps->phases.push_back(ph);
+      d.nphases++;
+    };
+    auto push_rop = [&](const ROp &r) {
+      ps->rops.push_back(r);
+      ps->phases.back().nops++;
+    };
+    bool last_is_diag = false;  // the last phase is a diagonal-only phase
+    auto flush = [&](std::vector<const Op *> &gates) {
+      if (gates.empty()) return true;
+      last_is_diag = false;
+      std::vector<std::pair<int, int>> pairs;
+      for (const Op *g : gates) pairs.push_back({g->u, g->v});
+      Plan pp;
+      if (!build_plan(K, pairs, kRegBits, 0, &pp, err)) return false;
+      for (int k = 0; k < pp.segments(); ++k) {
+        new_phase(pp.segQ[k]);
+        const std::vector<int> &rb = pp.segQ[k];
+        for (const PlanGate &g : pp.seg[k]) {
+          int ku = (int)(std::find(rb.begin(), rb.end(), g.i) - rb.begin());
+          int kv = (int)(std::find(rb.begin(), rb.end(), g.j) - rb.begin());
+          if (ku > kv) std::swap(ku, kv);
+          static const int base_idx[4] = {0, 4, 7, 9};  // combo = index of (ku,kv) in lexicographic order
+          ROp r{};
+          r.kind = OP_GATE;
+          r.combo = (uint8_t)(base_idx[ku] + (kv - ku - 1));
+          r.coef = gates[g.bond]->coef;
+          push_rop(r);
+        }
+      }
+      gates.clear();
+      return true;
+    };
+    std::vector<const Op *> gates;
+    for (int k = 0; k < d.nops; ++k) {
+      const Op &op = ps->ops[d.op0 + k];
+      if (op.kind == OP_GATE) {
+        gates.push_back(&op);
+        continue;
+      }
+      if (!flush(gates)) return false;
+      ROp r{};
+      r.kind = op.kind;
+      r.arg = op.arg;
+      if (op.kind == OP_DIAG) {
+        // the diagonal phase runs alone (its own phase, no register subcube)
+        if (!pending.empty()) new_phase({0, 1, 2, 3, 4});
+        pending.push_back(r);
+        new_phase({0, 1, 2, 3, 4});
+        last_is_diag = true;
+      } else if (d.nphases > 0 && pending.empty() && !last_is_diag) {
+        push_rop(r);
+      } else {
+        pending.push_back(r);
+      }
+    }
+    if (!flush(gates)) return false;
+    if (!pending.empty() || d.nphases == 0) new_phase({0, 1, 2, 3, 4});
+  }
+  return true;
+}
+
+static int plan_state(const spinrp_system &sys, int prec, Plan *plan, PassSet *ps, int *max_blocks) {
+  int rc = make_plan(sys, prec, plan);
+  if (rc) return rc;
+  build_passes(*plan, any_diag(sys), ps);
+  if (use_phases(prec, plan->K)) {
+    std::string err;
+    if (!compile_phases(ps, plan->K, &err)) return fail(SPINRP_EINVAL, "phases: %s", err.c_str());
+  }
+  // every gate on two distinct bits of its tile; every store permutation a permutation
+  for (const PassDesc &d : ps->desc) {
+    unsigned seen = 0;
+    for (int q = 0; q < d.K; ++q) seen |= 1u << d.perm[q];
+    if (d.K != plan->K || seen != (1u << d.K) - 1u)
+      return fail(SPINRP_EINVAL, "plan: inconsistent store permutation");
+    for (int k = 0; k < d.nops; ++k) {
+      const Op &op = ps->ops[d.op0 + k];
+      if (op.kind == OP_GATE && (op.u >= d.K || op.v >= d.K || op.u == op.v))
+        return fail(SPINRP_EINVAL, "plan: gate outside its tile");
+    }
+  }
+  *max_blocks = std::max(init_blocks(sys.M), 1 << (sys.M - plan->K));
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_state_bytes(const spinrp_system *sys, int prec, int64_t series_cap,
+                                  size_t *psi_bytes, size_t *work_bytes) {
+  if (!sys || (prec != SPINRP_C64 && prec != SPINRP_C128) || series_cap < 1)
+    return fail(SPINRP_EINVAL, "state_bytes: bad argument");
+  Plan plan;
+  PassSet ps;
+  int mb = 0;
+  int rc = plan_state(*sys, prec, &plan, &ps, &mb);
+  if (rc) return rc;
+  const size_t amp = prec == SPINRP_C64 ? 8 : 16;
+  if (psi_bytes) *psi_bytes = amp << sys->M;
+  if (work_bytes)
+    *work_bytes = work_layout(sys->M, (int)sys->bonds.size(), series_cap, ps, mb).total;
+  return SPINRP_OK;
+}
+
+static void free_state(spinrp_state *st) {
+  if (!st) return;
+  prof_clear(st);
+  if (st->own_psi && st->psi) cudaFree(st->psi);
+  if (st->own_work && st->work) cudaFree(st->work);
+  delete st;
+}
+
+template <typename R>
+static int set_smem_limits() {
+  // the widest tile of this precision (2^14 c64 or 2^13 c128 = 128 KiB)
+  const int kmax = sizeof(R) == 4 ? 14 : 13;
+  CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(typename CT<R>::T) << kmax)));
+  if (sizeof(R) == 4)
+    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_state_create(const spinrp_system *sys, int prec, void *stream,
+                                   int64_t series_cap, void *psi, void *work, spinrp_state **out) {
+  if (!out) return fail(SPINRP_EINVAL, "state_create: out is NULL");
+  *out = nullptr;
+  if (!sys || (prec != SPINRP_C64 && prec != SPINRP_C128) || series_cap < 1)
+    return fail(SPINRP_EINVAL, "state_create: bad argument");
+  if (((uintptr_t)psi & 255) || ((uintptr_t)work & 255))
+    return fail(SPINRP_EINVAL, "state_create: buffers must be 256-byte aligned");
+  spinrp_state *st = new (std::nothrow) spinrp_state;
+  if (!st) return fail(SPINRP_ENOMEM, "state_create: out of host memory");
+  st->M = sys->M;
+  st->prec = prec;
+  st->stream = (cudaStream_t)stream;
+  st->cap = series_cap;
+  st->nb = (int)sys->bonds.size();
+  st->has_diag = any_diag(*sys);
+  int rc = plan_state(*sys, prec, &st->plan, &st->ps, &st->max_blocks);
+  if (rc) {
+    delete st;
+    return rc;
+  }
+  st->lay = work_layout(st->M, st->nb, series_cap, st->ps, st->max_blocks);
+  for (auto &bd : sys->bonds) st->bvals.push_back(sys->b[bd.first * sys->M + bd.second]);
+  st->a = sys->a;
+  st->logical_of.assign(st->M, 0);
+  for (int q = 0; q < st->M; ++q) st->logical_of[st->plan.pos[q]] = (uint8_t)q;
+
+  cudaError_t e = cudaGetDevice(&st->device);
+  if (e != cudaSuccess) {
+    delete st;
+    return fail(SPINRP_ECUDA, "state_create: cudaGetDevice: %s", cudaGetErrorString(e));
+  }
+  const size_t psi_bytes = (prec == SPINRP_C64 ? size_t(8) : size_t(16)) << st->M;
+  if (psi) {
+    st->psi = psi;
+  } else {
+    e = cudaMalloc(&st->psi, psi_bytes);
+    if (e != cudaSuccess) {
+      delete st;
+      cudaGetLastError();
+      return fail(SPINRP_ENOMEM, "state_create: cudaMalloc(%zu): %s", psi_bytes, cudaGetErrorString(e));
+    }
+    st->own_psi = true;
+  }
+  if (work) {
+    st->work = (unsigned char *)work;
+  } else {
+    e = cudaMalloc((void **)&st->work, st->lay.total);
+    if (e != cudaSuccess) {
+      free_state(st);
+      cudaGetLastError();
+      return fail(SPINRP_ENOMEM, "state_create: cudaMalloc(%zu): %s", st->lay.total, cudaGetErrorString(e));
+    }
+    st->own_work = true;
+  }
+  unsigned char *w = st->work;
+  st->series = (double *)(w + st->lay.series);
+  st->partials = (double2 *)(w + st->lay.partials);
+  st->ticket = (unsigned *)(w + st->lay.ticket);
+  st->coefs = (GateCoef *)(w + st->lay.coefs);
+  st->d_bvals = (double *)(w + st->lay.bvals);
+  st->d_a = (double *)(w + st->lay.adiag);
+  st->qdiag = (uint64_t *)(w + st->lay.qdiag);
+  st->passes = (PassDesc *)(w + st->lay.passes);
+  st->ops = (Op *)(w + st->lay.ops);
+  st->phases = (PhaseDesc *)(w + st->lay.phases);
+  st->rops = (ROp *)(w + st->lay.rops);
+  st->v2 = use_phases(prec, st->plan.K);
+  st->stage = (double2 *)(w + st->lay.stage);
+  st->stage_idx = (int64_t *)(w + st->lay.stage_idx);
+
+  auto up = [&](void *dst, const void *src, size_t n) -> cudaError_t {
+    if (n == 0) return cudaSuccess;
+    st->h2d += (int64_t)n;
+    return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st->stream);
+  };
+  if ((e = cudaMemsetAsync(st->ticket, 0, 256, st->stream)) != cudaSuccess ||
+      (e = up(st->d_bvals, st->bvals.data(), sizeof(double) * st->bvals.size())) != cudaSuccess ||
+      (e = up(st->d_a, st->a.data(), sizeof(double) * st->a.size())) != cudaSuccess ||
+      (e = up(st->passes, st->ps.desc.data(), sizeof(PassDesc) * st->ps.desc.size())) != cudaSuccess ||
+      (e = up(st->ops, st->ps.ops.data(), sizeof(Op) * st->ps.ops.size())) != cudaSuccess ||
+      (e = up(st->phases, st->ps.phases.data(), sizeof(PhaseDesc) * st->ps.phases.size())) != cudaSuccess ||
+      (e = up(st->rops, st->ps.rops.data(), sizeof(ROp) * st->ps.rops.size())) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st->stream)) != cudaSuccess) {
+    free_state(st);
+    return fail(SPINRP_ECUDA, "state_create: upload: %s", cudaGetErrorString(e));
+  }
+  rc = prec == SPINRP_C64 ? set_smem_limits<float>() : set_smem_limits<double>();
+  if (rc) {
+    free_state(st);
+    return rc;
+  }
+  *out = st;
+  return SPINRP_OK;
+}
+
+extern "C" void spinrp_state_destroy(spinrp_state *st) {
+  if (!st) return;
+  cudaStreamSynchronize(st->stream);
+  free_state(st);
+}
+
+static LayoutArg layout_arg(const spinrp_state *st) {
+  LayoutArg la;
+  memset(&la, 0, sizeof la);
+  for (int p = 0; p < st->M; ++p) la.logical_of[p] = st->logical_of[p];
+  return la;
+}
+
+extern "C" int spinrp_state_init_random_phase(spinrp_state *st, uint64_t seed) {
+  if (!st) return fail(SPINRP_EINVAL, "init: state is NULL");
+  const int blocks = init_blocks(st->M);
+  prof_mark(st, SPINRP_KERNEL_INIT);
+  ++g_launches;
+  if (st->prec == SPINRP_C64)
+    init_kernel<float><<<blocks, 256, 0, st->stream>>>((float2 *)st->psi, st->M, layout_arg(st), seed,
+                                                        st->partials, st->ticket, st->series, 0);
+  else
+    init_kernel<double><<<blocks, 256, 0, st->stream>>>((double2 *)st->psi, st->M, layout_arg(st), seed,
+                                                         st->partials, st->ticket, st->series, 0);
+  CUDA_TRY(cudaGetLastError());
+  prof_mark(st, SPINRP_KERNEL_INIT);
+  st->len = 1;
+  st->ready = true;
+  return SPINRP_OK;
+}
+
+// physical index of logical basis index x
+static int64_t to_physical(const spinrp_state *st, int64_t x) {
+  int64_t y = 0;
+  for (int q = 0; q < st->M; ++q) y |= ((x >> q) & 1) << st->plan.pos[q];
+  return y;
+}
+
+extern "C" int spinrp_state_load(spinrp_state *st, const double *amps) {
+  if (!st || !amps) return fail(SPINRP_EINVAL, "load: bad argument");
+  const int64_t N = int64_t(1) << st->M;
+  std::vector<int64_t> idx;
+  for (int64_t k0 = 0; k0 < N; k0 += kStage) {
+    const int64_t n = std::min(kStage, N - k0);
+    idx.resize(n);
+    for (int64_t k = 0; k < n; ++k) idx[k] = to_physical(st, k0 + k);
+    CUDA_TRY(cudaMemcpyAsync(st->stage_idx, idx.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st->stream));
+    CUDA_TRY(cudaMemcpyAsync(st->stage, amps + 2 * k0, sizeof(double2) * n, cudaMemcpyHostToDevice, st->stream));
+    st->h2d += (int64_t)(sizeof(int64_t) + sizeof(double2)) * n;
+    ++g_launches;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
+    if (st->prec == SPINRP_C64)
+      scatter_kernel<float><<<blocks, 256, 0, st->stream>>>((float2 *)st->psi, st->stage_idx, n, st->stage);
+    else
+      scatter_kernel<double><<<blocks, 256, 0, st->stream>>>((double2 *)st->psi, st->stage_idx, n, st->stage);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(st->stream));
+  }
+  const int blocks = init_blocks(st->M);
+  ++g_launches;
+  if (st->prec == SPINRP_C64)
+    observe_kernel<float><<<blocks, 256, 0, st->stream>>>((const float2 *)st->psi, st->M, st->plan.pos[0],
+                                                           st->partials, st->ticket, st->series, 0);
+  else
+    observe_kernel<double><<<blocks, 256, 0, st->stream>>>((const double2 *)st->psi, st->M, st->plan.pos[0],
+                                                            st->partials, st->ticket, st->series, 0);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(st->stream));
+  st->len = 1;
+  st->ready = true;
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_state_read(spinrp_state *st, const int64_t *idx, int64_t n, double *out) {
+  if (!st || n < 0 || (n > 0 && (!idx || !out))) return fail(SPINRP_EINVAL, "read: bad argument");
+  const int64_t N = int64_t(1) << st->M;
+  std::vector<int64_t> pidx;
+  for (int64_t k0 = 0; k0 < n; k0 += kStage) {
+    const int64_t m = std::min(kStage, n - k0);
+    pidx.resize(m);
+    for (int64_t k = 0; k < m; ++k) {
+      if (idx[k0 + k] < 0 || idx[k0 + k] >= N) return fail(SPINRP_EINVAL, "read: index out of range");
+      pidx[k] = to_physical(st, idx[k0 + k]);
+    }
+    CUDA_TRY(cudaMemcpyAsync(st->stage_idx, pidx.data(), sizeof(int64_t) * m, cudaMemcpyHostToDevice, st->stream));
+    st->h2d += (int64_t)sizeof(int64_t) * m;
+    st->d2h += (int64_t)sizeof(double2) * m;
+    ++g_launches;
+    const int blocks = (int)std::min<int64_t>((m + 255) / 256, 1024);
+    if (st->prec == SPINRP_C64)
+      gather_kernel<float><<<blocks, 256, 0, st->stream>>>((const float2 *)st->psi, st->stage_idx, m, st->stage);
+    else
+      gather_kernel<double><<<blocks, 256, 0, st->stream>>>((const double2 *)st->psi, st->stage_idx, m, st->stage);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(out + 2 * k0, st->stage, sizeof(double2) * m, cudaMemcpyDeviceToHost, st->stream));
+    CUDA_TRY(cudaStreamSynchronize(st->stream));
+  }
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_state_layout(const spinrp_state *st, int32_t *layout, void **psi) {
+  if (!st) return fail(SPINRP_EINVAL, "layout: state is NULL");
+  if (layout)
+    for (int q = 0; q < st->M; ++q) layout[q] = st->plan.pos[q];
+  if (psi) *psi = st->psi;
+  return SPINRP_OK;
+}
+
+template <typename R>
+static int launch_pass(spinrp_state *st, int pass, int64_t slot) {
+  const int K = st->plan.K;
+  const int nt = std::min(512, std::max(32, 1 << K));
+  const size_t smem = sizeof(typename CT<R>::T) << K;
+  const unsigned blocks = 1u << (st->M - K);
+  prof_mark(st, SPINRP_KERNEL_SWEEP);
+  ++g_launches;
+  if (sizeof(R) == 4 && st->v2) {
+    sweep2_kernel<<<blocks, 1 << (K - 5), size_t(8) << K, st->stream>>>(
+        (float2 *)st->psi, st->passes + pass, st->phases, st->rops, st->coefs, st->qdiag, st->M,
+        st->partials, st->ticket, st->series, slot);
+    CUDA_TRY(cudaGetLastError());
+    prof_mark(st, SPINRP_KERNEL_SWEEP);
+    return SPINRP_OK;
+  }
+  sweep_kernel<R><<<blocks, nt, smem, st->stream>>>(
+      (typename CT<R>::T *)st->psi, st->passes + pass, st->ops, st->coefs, st->qdiag, st->M,
+      st->partials, st->ticket, st->series, slot);
+  CUDA_TRY(cudaGetLastError());
+  prof_mark(st, SPINRP_KERNEL_SWEEP);
+  return SPINRP_OK;
+}
+
+template <typename R>
+static int run_evolve(spinrp_state *st, int64_t steps) {
+  const PassSet &ps = st->ps;
+  int64_t slot = st->len;  // slot of the P recorded after the next step
+#define RUN(pass, sl)                                  \
+  do {                                                 \
+    int rc_ = launch_pass<R>(st, (pass), (sl));        \
+    if (rc_) return rc_;                               \
+  } while (0)
+  if (st->plan.segments() == 1) {
+    if (steps == 1) {
+      RUN(ps.only, slot);
+    } else {
+      RUN(ps.first, slot++);
+      for (int64_t n = 1; n + 1 < steps; ++n) RUN(ps.midstep, slot++);
+      RUN(ps.last, slot);
+    }
+  } else {
+    RUN(ps.head, -1);
+    for (int64_t n = 0; n < steps; ++n) {
+      for (int id : ps.body) RUN(id, -1);
+      RUN(ps.mid, -1);
+      for (int id : ps.bodyr) RUN(id, -1);
+      RUN(n + 1 < steps ? ps.join : ps.tail, slot++);
+    }
+  }
+#undef RUN
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_evolve(spinrp_state *st, double dt, int64_t steps, int order) {
+  if (!st) return fail(SPINRP_EINVAL, "evolve: state is NULL");
+  if (order != 2) return fail(SPINRP_EUNSUPPORTED, "evolve: only order 2 is implemented");
+  if (!st->ready) return fail(SPINRP_ESTATE, "evolve: state not initialized");
+  if (!std::isfinite(dt)) return fail(SPINRP_EINVAL, "evolve: dt not finite");
+  if (steps < 0) return fail(SPINRP_EINVAL, "evolve: negative steps");
+  if (steps == 0) return SPINRP_OK;
+  if (st->len + steps > st->cap)
+    return fail(SPINRP_EINVAL, "evolve: series capacity %lld exceeded", (long long)st->cap);
+  if (!(dt == st->coef_dt)) {
+    prof_mark(st, SPINRP_KERNEL_TABLES);
+    if (st->nb > 0) {
+      ++g_launches;
+      coef_kernel<<<(2 * st->nb + 127) / 128, 128, 0, st->stream>>>(st->d_bvals, st->nb, dt, st->coefs);
+      CUDA_TRY(cudaGetLastError());
+    }
+    if (st->has_diag) {
+      const int n = 2 * st->M * st->M;
+      ++g_launches;
+      diag_kernel<<<(n + 127) / 128, 128, 0, st->stream>>>(st->d_a, layout_arg(st), st->M, dt, st->qdiag);
+      CUDA_TRY(cudaGetLastError());
+    }
+    prof_mark(st, SPINRP_KERNEL_TABLES);
+    st->coef_dt = dt;
+  }
+  int rc = st->prec == SPINRP_C64 ? run_evolve<float>(st, steps) : run_evolve<double>(st, steps);
+  if (rc) return rc;
+  st->len += steps;
+  return SPINRP_OK;
+}
+
+extern "C" int64_t spinrp_series_length(const spinrp_state *st) { return st ? st->len : 0; }
+
+static int copy_series(spinrp_state *st, int which, double *out, int64_t cap, int64_t *n) {
+  if (!st || !n || (cap > 0 && !out)) return fail(SPINRP_EINVAL, "series: bad argument");
+  *n = st->len;
+  const int64_t m = std::min(cap, st->len);
+  if (m <= 0) return SPINRP_OK;
+  std::vector<double> buf(2 * m);
+  CUDA_TRY(cudaMemcpyAsync(buf.data(), st->series, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, st->stream));
+  st->d2h += (int64_t)sizeof(double) * 2 * m;
+  CUDA_TRY(cudaStreamSynchronize(st->stream));
+  for (int64_t k = 0; k < m; ++k) out[k] = buf[2 * k + which];
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_polarization(spinrp_state *st, int site, double *out, int64_t cap, int64_t *n) {
+  if (st && site != 1)
+    return fail(SPINRP_EUNSUPPORTED, "polarization: only site 1 is recorded (got %d)", site);
+  return copy_series(st, 0, out, cap, n);
+}
+
+extern "C" int spinrp_norm_series(spinrp_state *st, double *out, int64_t cap, int64_t *n) {
+  return copy_series(st, 1, out, cap, n);
+}
+
+extern "C" int spinrp_profile(spinrp_state *st, int enable) {
+  if (!st) return fail(SPINRP_EINVAL, "profile: state is NULL");
+  if (enable) {
+    cudaStreamSynchronize(st->stream);
+    prof_clear(st);
+  }
+  st->prof = enable != 0;
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_profile_read(spinrp_state *st, int kind, double *total_ms, int64_t *launches) {
+  if (!st || kind < 0 || kind > 2) return fail(SPINRP_EINVAL, "profile_read: bad argument");
+  CUDA_TRY(cudaStreamSynchronize(st->stream));
+  const auto &v = st->ev[kind];
+  double ms = 0.0;
+  for (size_t k = 0; k + 1 < v.size(); k += 2) {
+    float t = 0.0f;
+    CUDA_TRY(cudaEventElapsedTime(&t, v[k], v[k + 1]));
+    ms += t;
+  }
+  if (total_ms) *total_ms = ms;
+  if (launches) *launches = (int64_t)(v.size() / 2);
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_state_transfer_bytes(const spinrp_state *st, int64_t *h2d, int64_t *d2h) {
+  if (!st) return fail(SPINRP_EINVAL, "transfer_bytes: state is NULL");
+  if (h2d) *h2d = st->h2d;
+  if (d2h) *d2h = st->d2h;
+  return SPINRP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// host self-check of the register-blocked programs
+// ---------------------------------------------------------------------------
+#include <complex>
+#include <random>
+
+namespace {
+using cplx = std::complex<double>;
+
+void check_rotate(std::vector<cplx> &A, int u, int v, int coef) {
+  const double th = 0.1 + 0.013 * coef, c = std::cos(th), s = std::sin(th);
+  const size_t T = A.size();
+  for (size_t t = 0; t < T; ++t) {
+    if (((t >> u) & 1) != 1 || ((t >> v) & 1) != 0) continue;
+    const size_t w = t ^ (size_t(1) << u) ^ (size_t(1) << v);
+    const cplx a = A[t], b = A[w];
+    A[t] = c * a - cplx(0, s) * b;
+    A[w] = c * b - cplx(0, s) * a;
+  }
+}
+void check_diag(std::vector<cplx> &A, int arg) {
+  for (size_t t = 0; t < A.size(); ++t) {
+    const double ph = 0.3 * double((t * 2654435761u) % 1000u) / 1000.0 + 0.7 * arg;
+    A[t] *= cplx(std::cos(ph), std::sin(ph));
+  }
+}
+double check_reduce(const std::vector<cplx> &A) {
+  double r = 0.0;
+  for (size_t t = 0; t < A.size(); ++t) r += std::norm(A[t]) * double(t % 7 + 1);
+  return r;
+}
+}  // namespace
+
+extern "C" int spinrp_system_plan_check(const spinrp_system *sys, int prec, double *phases_per_sweep,
+                                        double *gates_per_phase) {
+  if (!sys || (prec != SPINRP_C64 && prec != SPINRP_C128))
+    return fail(SPINRP_EINVAL, "plan_check: bad argument");
+  Plan plan;
+  PassSet ps;
+  int mb = 0;
+  int rc = plan_state(*sys, prec, &plan, &ps, &mb);
+  if (rc) return rc;
+  if (phases_per_sweep) *phases_per_sweep = 0.0;
+  if (gates_per_phase) *gates_per_phase = 0.0;
+  const int K = plan.K;
+  if (!use_phases(prec, K)) return SPINRP_OK;
+  const size_t T = size_t(1) << K;
+  std::mt19937_64 rng(12345);
+  std::normal_distribution<double> nd;
+  long nphase = 0, ngate_phase = 0, ngates = 0;
+  for (size_t pi = 0; pi < ps.desc.size(); ++pi) {
+    const PassDesc &d = ps.desc[pi];
+    std::vector<cplx> A(T), B;
+    for (auto &x : A) x = cplx(nd(rng), nd(rng));
+    B = A;
+    std::vector<double> ra, rb;
+    for (int k = 0; k < d.nops; ++k) {
+      const Op &op = ps.ops[d.op0 + k];
+      if (op.kind == OP_GATE) check_rotate(A, op.u, op.v, op.coef);
+      else if (op.kind == OP_DIAG) check_diag(A, op.arg);
+      else ra.push_back(check_reduce(A));
+    }
+    static const int KU[10] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 3}, KV[10] = {1, 2, 3, 4, 2, 3, 4, 3, 4, 4};
+    for (int p = 0; p < d.nphases; ++p) {
+      const PhaseDesc &ph = ps.phases[d.phase0 + p];
+      uint32_t seen = 0;
+      for (int k = 0; k < kRegBits; ++k) seen |= 1u << ph.rb[k];
+      for (int k = 0; k < 5; ++k) seen |= 1u << ph.lanes[k];
+      for (int k = 0; k < K - 10; ++k) seen |= 1u << ph.warps[k];
+      if (seen != (1u << K) - 1u || __builtin_popcount(seen) != K)
+        return fail(SPINRP_EINVAL, "plan_check: pass %zu phase %d does not partition the tile bits", pi, p);
+      int g = 0;
+      for (int k = 0; k < ph.nops; ++k) {
+        const ROp &r = ps.rops[ph.op0 + k];
+        if (r.kind == OP_GATE) {
+          check_rotate(B, ph.rb[KU[r.combo]], ph.rb[KV[r.combo]], r.coef);
+          ++g;
+        } else if (r.kind == OP_DIAG) {
+          if (ph.nops != 1) return fail(SPINRP_EINVAL, "plan_check: diagonal op shares a phase");
+          check_diag(B, r.arg);
+        } else {
+          rb.push_back(check_reduce(B));
+        }
+      }
+      ++nphase;
+      if (g) ++ngate_phase, ngates += g;
+    }
+    double err = 0.0, ref = 0.0;
+    for (size_t t = 0; t < T; ++t) err = std::max(err, std::abs(A[t] - B[t])), ref = std::max(ref, std::abs(A[t]));
+    if (!(err <= 1e-10 * ref)) return fail(SPINRP_EINVAL, "plan_check: pass %zu differs (%.3e)", pi, err);
+    if (ra.size() != rb.size()) return fail(SPINRP_EINVAL, "plan_check: pass %zu reductions differ", pi);
+    for (size_t k = 0; k < ra.size(); ++k)
+      if (std::abs(ra[k] - rb[k]) > 1e-9 * std::abs(ra[k]))
+        return fail(SPINRP_EINVAL, "plan_check: pass %zu reduction %zu at a different point", pi, k);
+  }
+  if (phases_per_sweep) *phases_per_sweep = ps.desc.empty() ? 0.0 : double(nphase) / ps.desc.size();
+  if (gates_per_phase) *gates_per_phase = ngate_phase ? double(ngates) / ngate_phase : 0.0;
+  return SPINRP_OK;
+}

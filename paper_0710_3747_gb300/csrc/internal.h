@@ -1,0 +1,103 @@
+// internal.h -- structures shared by the host planner and the device kernels.
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+namespace spinrp {
+
+constexpr int kMaxM = 34;   // largest system (2^34 c64 amplitudes = 128 GiB)
+constexpr int kMaxK = 14;   // widest shared-memory tile (2^14 c64 = 128 KiB)
+
+enum OpKind : uint8_t {
+  OP_GATE = 1,    // flip-flop gate on tile-local bits (u, v), coefficient index `coef`
+  OP_DIAG = 2,    // e^{-i tau D} on every amplitude of the tile, tau variant `arg`
+  OP_REDUCE = 3,  // accumulate N_up / N_dn of the readout spin into this pass's slot
+};
+
+// One operation of a sweep, in tile-local bit indices.
+struct Op {
+  uint8_t kind;
+  uint8_t u, v;   // tile-local bits of a gate
+  uint8_t arg;    // diagonal variant (0: dt/2, 1: dt)
+  int32_t coef;   // gate coefficient index = 2*bond + variant (0: dt/2, 1: dt)
+};
+
+// Descriptor of one sweep ("pass") over the whole state: the state is cut into
+// 2^(M-K) tiles of 2^K amplitudes; tile-local bit q sits at physical bit
+// position tile_pos[q] (ascending, so tile bits 0..c-1 are the contiguous low
+// bits), the block index supplies the remaining bits at outer_pos[].
+struct PassDesc {
+  int32_t K;
+  int32_t nops;
+  int32_t op0;          // first op in the global op array
+  int32_t site_tile;    // tile-local bit of the readout spin, or -1 when it is an outer bit
+  int32_t site_pos;     // physical position of the readout spin
+  int32_t has_reduce;
+  int32_t relabel;      // nonzero when the tile is written back with permuted bits
+  uint8_t tile_pos[kMaxK];
+  uint8_t outer_pos[kMaxM];
+  uint8_t perm[kMaxK];  // store: output tile bit q takes the amplitude bit of input tile bit perm[q]
+  int32_t phase0;       // register-blocked program (complex64 path): first phase
+  int32_t nphases;      //   and number of phases
+};
+
+// Register-blocked execution of a pass (complex64 path).  In a phase every
+// thread holds the 2^5 amplitudes of the tile that differ only in the five
+// tile bits rb[] (its "subcube"), applies the phase's ops to them in registers
+// and writes them back to shared memory.  lanes[]/warps[] give the tile bits
+// the thread index supplies.
+constexpr int kRegBits = 5;
+struct PhaseDesc {
+  uint8_t rb[kRegBits];
+  uint8_t lanes[5];
+  uint8_t warps[kMaxK - 10];
+  uint8_t nops;
+  uint8_t pad;
+  int32_t op0;
+};
+
+// Op of a phase: GATE acts on register bits given by `combo` (pair index
+// 0..9 of (ku < kv) in lexicographic order); DIAG / REDUCE as in Op.
+struct ROp {
+  uint8_t kind;
+  uint8_t combo;
+  uint8_t arg;
+  uint8_t pad;
+  int32_t coef;
+};
+
+// Gate coefficients of exp(-i theta sigma_x) on a flip-flop pair, theta = b tau/2,
+// stored as (cos theta - 1, sin theta) so that small rotations keep their
+// relative precision: x' = x + cm1 x - i s y.
+struct GateCoef {
+  double cm1, s;
+  float cm1f, sf;
+};
+
+// ---------------------------------------------------------------------------
+// Host plan
+// ---------------------------------------------------------------------------
+struct PlanGate {
+  int bond;   // index into the canonical bond list
+  int i, j;   // logical spins (0-based)
+};
+
+struct Plan {
+  int M = 0, K = 0, c = 0;
+  std::vector<int> pos;                      // logical spin -> physical bit position
+  std::vector<std::vector<PlanGate>> seg;    // forward half step cut into segments
+  std::vector<std::vector<int>> segQ;        // logical spins of each segment's tile
+  std::vector<std::vector<int>> exitX;       // spins moved into the low bits after segment k
+  int segments() const { return (int)seg.size(); }
+  int sweeps_per_step() const { return seg.size() <= 1 ? 1 : 2 * (int)seg.size() - 2; }
+};
+
+// Build the plan for the canonical bonds with tiles of K spins whose lowest c
+// physical bits are shared by every tile.  Returns false and sets *err on failure.
+bool build_plan(int M, const std::vector<std::pair<int, int>> &bonds, int K, int c, Plan *plan,
+                std::string *err);
+
+}  // namespace spinrp

@@ -1,0 +1,656 @@
+// kernels.cuh -- device code of the random-phase Trotter path (sm_103a).
+//
+//   init_kernel   : the paper's entangled random-phase state, phases from an
+//                   in-kernel Philox4x32-10, fused P(0)/norm reduction.
+//   coef_kernel   : FP64 generation of every flip-flop gate's (cos-1, sin) pair
+//                   for dt/2 and dt, rounded to FP32 with a unitarity-defect search.
+//   diag_kernel   : FP64 -> 64-bit fixed-point turn tables of e^{-i tau a_ij/4 s s}.
+//   sweep_kernel  : one pass over the whole state in shared-memory tiles of 2^K
+//                   amplitudes: applies the pass's gates, the diagonal phase and
+//                   the polarization reduction, then writes the tile back.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace spinrp {
+
+template <typename R> struct CT;
+template <> struct CT<float> { using T = float2; };
+template <> struct CT<double> { using T = double2; };
+
+struct LayoutArg {
+  uint8_t logical_of[kMaxM];  // physical bit position -> logical spin
+};
+
+__device__ __forceinline__ uint64_t deposit_bits(uint64_t v, const uint8_t *pos, int n) {
+  uint64_t r = 0;
+  for (int k = 0; k < n; ++k) r |= ((v >> k) & 1ull) << pos[k];
+  return r;
+}
+
+// Insert a zero bit at position b of x.
+__device__ __forceinline__ uint32_t insert_zero(uint32_t x, int b) {
+  return ((x >> b) << (b + 1)) | (x & ((1u << b) - 1u));
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds of two 32x32
+// multiplies (multipliers 0xD2511F53, 0xCD9E8D57) mixed with the counter and a
+// key bumped by the Weyl constants 0x9E3779B9, 0xBB67AE85.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// e^{2 pi i theta / 2^64} for a 64-bit fixed-point turn count theta.
+__device__ __forceinline__ double2 cis_turns(uint64_t theta, double) {
+  const double turns = (double)(int64_t)theta * 5.421010862427522e-20;  // 2^-64
+  double s, c;
+  sincospi(2.0 * turns, &s, &c);
+  return make_double2(c, s);
+}
+// FP32 version: split off the nearest quarter turn exactly in integers, take
+// sin/cos of the remainder (|r| <= 1/8 turn, so float keeps ~2^-27 turn
+// absolute precision) and rotate by the quarter turns.
+__device__ __forceinline__ float2 cis_turns(uint64_t theta, float) {
+  const int64_t h = (int64_t)(int32_t)(uint32_t)(theta >> 32);  // turns * 2^32, signed
+  const int64_t k = (h + (1ll << 29)) >> 30;                     // nearest quarter turn
+  const int32_t r = (int32_t)(h - (k << 30));                    // |r| <= 2^29
+  float s, c;
+  sincospif((float)r * 4.656612873077393e-10f, &s, &c);          // angle = pi * r * 2^-31
+  switch ((int)(k & 3)) {
+    case 0: return make_float2(c, s);
+    case 1: return make_float2(-s, c);
+    case 2: return make_float2(-c, -s);
+    default: return make_float2(s, -c);
+  }
+}
+
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+
+// Deterministic grid reduction of (N_up, N_dn): block partials in FP64, the
+// last block to finish sums them in block order and writes (P, norm).
+__device__ void reduce_finalize(double up, double dn, double2 *partials, unsigned *ticket,
+                                double *series, int64_t slot) {
+  __shared__ double s_up[32], s_dn[32];
+  __shared__ int s_last;
+  for (int o = 16; o; o >>= 1) {
+    up += __shfl_xor_sync(0xffffffffu, up, o);
+    dn += __shfl_xor_sync(0xffffffffu, dn, o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) s_up[warp] = up, s_dn[warp] = dn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0, d = 0.0;
+    for (int w = 0; w < nw; ++w) u += s_up[w], d += s_dn[w];
+    partials[blockIdx.x] = make_double2(u, d);
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double u = 0.0, d = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    const double2 p = __ldcg(&partials[b]);
+    u += p.x, d += p.y;
+  }
+  for (int o = 16; o; o >>= 1) {
+    u += __shfl_xor_sync(0xffffffffu, u, o);
+    d += __shfl_xor_sync(0xffffffffu, d, o);
+  }
+  __syncthreads();
+  if (lane == 0) s_up[warp] = u, s_dn[warp] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double U = 0.0, D = 0.0;
+    for (int w = 0; w < nw; ++w) U += s_up[w], D += s_dn[w];
+    series[2 * slot] = (U - D) / (U + D);
+    series[2 * slot + 1] = U + D;
+    *ticket = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Random-phase initial state.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256)
+init_kernel(typename CT<R>::T *__restrict__ psi, int M, LayoutArg lay, uint64_t seed,
+            double2 *partials, unsigned *ticket, double *series, int64_t slot) {
+  using C = typename CT<R>::T;
+  const uint64_t N = 1ull << M;
+  const R amp = (R)exp2(-0.5 * (double)(M - 1));
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  R up = 0, dn = 0;
+  for (uint64_t y = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; y < N;
+       y += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t x = 0;
+    for (int p = 0; p < M; ++p) x |= ((y >> p) & 1ull) << lay.logical_of[p];
+    C v;
+    if ((x & 1ull) == 0) {
+      v.x = 0, v.y = 0;
+    } else {
+      const uint64_t r = x >> 1;
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)r, (uint32_t)(r >> 32), 0u, 0u), key);
+      const uint64_t bits = ((uint64_t)w.x << 32) | w.y;
+      C e;
+      if (sizeof(R) == 8) {
+        // u = top 53 bits * 2^-53 exactly as defined; angle 2 pi u
+        double s, c;
+        sincospi(2.0 * ((double)(bits >> 11) * 1.1102230246251565e-16), &s, &c);
+        e.x = (R)c, e.y = (R)s;
+      } else {
+        const float2 f = cis_turns(bits, 0.0f);
+        e.x = (R)f.x, e.y = (R)f.y;
+      }
+      v.x = amp * e.x, v.y = amp * e.y;
+      up += v.x * v.x + v.y * v.y;
+    }
+    psi[y] = v;
+  }
+  reduce_finalize((double)up, (double)dn, partials, ticket, series, slot);
+}
+
+// ---------------------------------------------------------------------------
+// Per-evolve FP64 tables.
+// ---------------------------------------------------------------------------
+__global__ void coef_kernel(const double *__restrict__ bvals, int nb, double dt,
+                            GateCoef *__restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= 2 * nb) return;
+  const double tau = (k & 1) ? dt : 0.5 * dt;
+  const double th = 0.5 * bvals[k >> 1] * tau;  // exp(-i tau b (SxSx+SySy)) = cos th - i sin th sigma_x
+  const double s = sin(th), h = sin(0.5 * th);
+  const double cm1 = -2.0 * h * h;  // cos th - 1 without cancellation
+  GateCoef g;
+  g.cm1 = cm1;
+  g.s = s;
+  // FP32 pair: among +-2 ulps of the rounded values, the one whose rotation is
+  // closest to unitary, |(1+c)^2 + s^2 - 1| = |2c + c^2 + s^2|.
+  const float c0 = (float)cm1, s0 = (float)s;
+  float bc = c0, bs = s0;
+  double best = fabs(2.0 * (double)c0 + (double)c0 * c0 + (double)s0 * s0);
+  for (int dc = -2; dc <= 2; ++dc)
+    for (int ds = -2; ds <= 2; ++ds) {
+      const float cf = (c0 == 0.0f) ? c0 : __int_as_float(__float_as_int(c0) + dc);
+      const float sf = (s0 == 0.0f) ? s0 : __int_as_float(__float_as_int(s0) + ds);
+      const double def = fabs(2.0 * (double)cf + (double)cf * cf + (double)sf * sf);
+      if (def < best) best = def, bc = cf, bs = sf;
+    }
+  g.cm1f = bc;
+  g.sf = bs;
+  out[k] = g;
+}
+
+// q[v][p][p'] (physical positions): turns of the pair phase -tau_v a_ij / 4 (the
+// phase of e^{-i tau a_ij s_i s_j} for s_i s_j = +1/4), as 64-bit fixed point.
+// tau_0 = dt/2, tau_1 = dt.
+__global__ void diag_kernel(const double *__restrict__ a, LayoutArg lay, int M, double dt,
+                            uint64_t *__restrict__ q) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= 2 * M * M) return;
+  const int v = k / (M * M), p = (k / M) % M, p2 = k % M;
+  uint64_t val = 0;
+  if (p != p2) {
+    const int i = lay.logical_of[p], j = lay.logical_of[p2];
+    const double aij = a[(i < j ? i : j) * M + (i < j ? j : i)];
+    const double tau = v ? dt : 0.5 * dt;
+    const double t = -tau * aij * 0.039788735772973836;  // 1/(8 pi)
+    const double f = t - rint(t);                          // [-1/2, 1/2] turns
+    val = ((uint64_t)llrint(f * 9.223372036854775808e18)) << 1;
+  }
+  q[k] = val;
+}
+
+// ---------------------------------------------------------------------------
+// One sweep.  Each block owns one tile: it loads the tile's 2^K amplitudes
+// into shared memory, applies the pass's ops in order and stores the tile.
+// ---------------------------------------------------------------------------
+// a' = a + cm1 a - i s b ; b' = b + cm1 b - i s a.
+// FP32: the small increment d = cm1 a - i s b is formed first and added to a
+// with a single rounding; rounding a(1 + cm1) on its own first biases |a|^2
+// upwards (measured: the norm grows ~1e-9 per gate application, linearly).
+template <typename R>
+__device__ __forceinline__ void rotate(typename CT<R>::T &a, typename CT<R>::T &b, R cm1, R s);
+
+template <>
+__device__ __forceinline__ void rotate<float>(float2 &a, float2 &b, float cm1, float s) {
+  const float ax = a.x, ay = a.y, bx = b.x, by = b.y;
+  a.x = ax + fmaf(cm1, ax, s * by);
+  a.y = ay + fmaf(cm1, ay, -s * bx);
+  b.x = bx + fmaf(cm1, bx, s * ay);
+  b.y = by + fmaf(cm1, by, -s * ax);
+}
+
+template <>
+__device__ __forceinline__ void rotate<double>(double2 &a, double2 &b, double cm1, double s) {
+  const double ax = a.x, ay = a.y, bx = b.x, by = b.y;
+  a.x = fma(s, by, fma(cm1, ax, ax));
+  a.y = fma(-s, bx, fma(cm1, ay, ay));
+  b.x = fma(s, ay, fma(cm1, bx, bx));
+  b.y = fma(-s, ax, fma(cm1, by, by));
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512)
+sweep_kernel(typename CT<R>::T *__restrict__ psi, const PassDesc *__restrict__ pdesc,
+             const Op *__restrict__ ops, const GateCoef *__restrict__ coefs,
+             const uint64_t *__restrict__ qdiag, int M, double2 *partials, unsigned *ticket,
+             double *series, int64_t slot) {
+  using C = typename CT<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *tile = reinterpret_cast<C *>(smem_raw);
+  __shared__ PassDesc d;
+  __shared__ uint64_t sH[kMaxK];
+  __shared__ uint64_t sQ[kMaxK * kMaxK];
+  __shared__ uint64_t sOut;
+  {
+    const int nwords = (int)(sizeof(PassDesc) / 4);
+    for (int w = threadIdx.x; w < nwords; w += blockDim.x)
+      reinterpret_cast<int *>(&d)[w] = reinterpret_cast<const int *>(pdesc)[w];
+  }
+  __syncthreads();
+  const int K = d.K;
+  const int nt = blockDim.x, tid = threadIdx.x;
+  const int lognt = 31 - __clz(nt);
+  const int L = lognt < K ? lognt : K;  // tile bits taken from the thread index
+  const uint32_t T = 1u << K;
+  const uint64_t base = deposit_bits(blockIdx.x, d.outer_pos, M - K);
+  const uint64_t off_lo = deposit_bits(tid, d.tile_pos, L);
+  auto offset = [&](uint32_t t) -> uint64_t {
+    uint64_t o = off_lo;
+    for (int q = L; q < K; ++q) o |= (uint64_t)((t >> q) & 1u) << d.tile_pos[q];
+    return o;
+  };
+  for (uint32_t t = tid; t < T; t += nt) tile[t] = psi[base + offset(t)];
+  __syncthreads();
+
+  R up = 0, dn = 0;
+  for (int k = 0; k < d.nops; ++k) {
+    const Op op = ops[d.op0 + k];
+    if (op.kind == OP_GATE) {
+      const GateCoef g = coefs[op.coef];
+      const R cm1 = sizeof(R) == 8 ? (R)g.cm1 : (R)g.cm1f;
+      const R s = sizeof(R) == 8 ? (R)g.s : (R)g.sf;
+      const int lo = op.u < op.v ? op.u : op.v, hi = op.u < op.v ? op.v : op.u;
+      const uint32_t bu = 1u << op.u, bv = 1u << op.v;
+      for (uint32_t p = tid; p < (T >> 2); p += nt) {
+        const uint32_t t0 = insert_zero(insert_zero(p, lo), hi);
+        C a = tile[t0 | bu], b = tile[t0 | bv];
+        rotate<R>(a, b, cm1, s);
+        tile[t0 | bu] = a;
+        tile[t0 | bv] = b;
+      }
+      __syncthreads();
+    } else if (op.kind == OP_DIAG) {
+      // Theta(x) = sum_{p<p'} q_pp' sigma_p sigma_p' (mod 2^64), split into
+      // outer-outer, outer-tile and tile-tile parts.
+      const uint64_t *q = qdiag + (size_t)op.arg * M * M;
+      const int nout = M - K;
+      if (tid < K) {
+        const int p = d.tile_pos[tid];
+        uint64_t h = 0;
+        for (int o = 0; o < nout; ++o) {
+          const int po = d.outer_pos[o];
+          const uint64_t v = q[p * M + po];
+          h += ((base >> po) & 1ull) ? v : (0ull - v);
+        }
+        sH[tid] = h;
+      } else if (tid == K) {
+        uint64_t s = 0;
+        for (int o = 0; o < nout; ++o)
+          for (int o2 = o + 1; o2 < nout; ++o2) {
+            const int p = d.outer_pos[o], p2 = d.outer_pos[o2];
+            const uint64_t v = q[p * M + p2];
+            s += (((base >> p) ^ (base >> p2)) & 1ull) ? (0ull - v) : v;
+          }
+        sOut = s;
+      }
+      for (int w = tid; w < K * K; w += nt) {
+        const int a = w / K, b = w % K;
+        sQ[w] = q[d.tile_pos[a] * M + d.tile_pos[b]];
+      }
+      __syncthreads();
+      // per-thread part: tile bits 0..L-1 come from tid
+      uint64_t thr = sOut;
+      for (int a = 0; a < L; ++a) {
+        const uint64_t ba = (tid >> a) & 1u;
+        thr += ba ? sH[a] : (0ull - sH[a]);
+        for (int b = a + 1; b < L; ++b)
+          thr += (ba ^ ((tid >> b) & 1u)) ? (0ull - sQ[a * K + b]) : sQ[a * K + b];
+      }
+      for (uint32_t t = tid; t < T; t += nt) {
+        uint64_t th = thr;
+        for (int a = L; a < K; ++a) {
+          const uint32_t ba = (t >> a) & 1u;
+          uint64_t f = sH[a];
+          for (int b = 0; b < L; ++b)
+            f += ((tid >> b) & 1u) ? sQ[b * K + a] : (0ull - sQ[b * K + a]);
+          th += ba ? f : (0ull - f);
+          for (int b = a + 1; b < K; ++b)
+            th += (ba ^ ((t >> b) & 1u)) ? (0ull - sQ[a * K + b]) : sQ[a * K + b];
+        }
+        const C e = cis_turns(th, (R)0);
+        tile[t] = cmul(tile[t], e);
+      }
+      __syncthreads();
+    } else if (op.kind == OP_REDUCE) {
+      for (uint32_t t = tid; t < T; t += nt) {
+        const C a = tile[t];
+        const R pr = a.x * a.x + a.y * a.y;
+        const uint64_t bit = d.site_tile >= 0 ? ((t >> d.site_tile) & 1u)
+                                              : ((base >> d.site_pos) & 1ull);
+        if (bit) up += pr;
+        else dn += pr;
+      }
+      __syncthreads();  // later ops overwrite the tile
+    }
+  }
+  if (!d.relabel) {
+    for (uint32_t t = tid; t < T; t += nt) psi[base + offset(t)] = tile[t];
+  } else {
+    // output tile bit q holds the spin that input tile bit perm[q] held
+    for (uint32_t t = tid; t < T; t += nt) {
+      uint32_t ti = 0;
+      for (int q = 0; q < K; ++q) ti |= ((t >> q) & 1u) << d.perm[q];
+      psi[base + offset(t)] = tile[ti];
+    }
+  }
+  if (d.has_reduce) reduce_finalize((double)up, (double)dn, partials, ticket, series, slot);
+}
+
+// Gather amplitudes at physical indices into a staging buffer (FP64 pairs).
+template <typename R>
+__global__ void gather_kernel(const typename CT<R>::T *__restrict__ psi,
+                              const int64_t *__restrict__ idx, int64_t n, double2 *out) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const typename CT<R>::T v = psi[idx[k]];
+    out[k] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
+template <typename R>
+__global__ void scatter_kernel(typename CT<R>::T *__restrict__ psi, const int64_t *__restrict__ idx,
+                               int64_t n, const double2 *__restrict__ in) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    typename CT<R>::T v;
+    v.x = (R)in[k].x;
+    v.y = (R)in[k].y;
+    psi[idx[k]] = v;
+  }
+}
+
+// Polarization/norm of the whole state (after a load).
+template <typename R>
+__global__ void __launch_bounds__(256)
+observe_kernel(const typename CT<R>::T *__restrict__ psi, int M, int site_pos, double2 *partials,
+               unsigned *ticket, double *series, int64_t slot) {
+  const uint64_t N = 1ull << M;
+  double up = 0, dn = 0;
+  for (uint64_t y = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; y < N;
+       y += (uint64_t)gridDim.x * blockDim.x) {
+    const typename CT<R>::T v = psi[y];
+    const double pr = (double)v.x * v.x + (double)v.y * v.y;
+    if ((y >> site_pos) & 1ull) up += pr;
+    else dn += pr;
+  }
+  reduce_finalize(up, dn, partials, ticket, series, slot);
+}
+
+// ===========================================================================
+// Register-blocked sweep (complex64).  The tile lives in shared memory with
+// an XOR swizzle; global<->shared copies are 16-byte cp.async loads and
+// 16-byte stores; between them the pass runs as a sequence of phases, each a
+// register-resident 32-amplitude subcube per thread (see PhaseDesc).
+// ===========================================================================
+namespace sw2 {
+
+// Shared-memory slot of tile index t: the low four bits are XORed with bits
+// 4-7, 8-11 and 12-15.  Linear over XOR, so slot(a ^ b) = slot(a) ^ slot(b);
+// lanes that differ in four tile bits of distinct residues mod 4 hit 16
+// distinct 8-byte bank pairs.
+__device__ __forceinline__ uint32_t slot(uint32_t t) {
+  return t ^ (((t >> 4) ^ (t >> 8) ^ (t >> 12)) & 15u);
+}
+
+template <int KU, int KV>
+__device__ __forceinline__ void gate_regs(float2 (&a)[32], float cm1, float s) {
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    if (((i >> KU) & 1) == 1 && ((i >> KV) & 1) == 0) {
+      const int j = i ^ (1 << KU) ^ (1 << KV);
+      rotate<float>(a[i], a[j], cm1, s);
+    }
+  }
+}
+
+__device__ __forceinline__ void gate_combo(float2 (&a)[32], int combo, float cm1, float s) {
+  switch (combo) {
+    case 0: gate_regs<0, 1>(a, cm1, s); break;
+    case 1: gate_regs<0, 2>(a, cm1, s); break;
+    case 2: gate_regs<0, 3>(a, cm1, s); break;
+    case 3: gate_regs<0, 4>(a, cm1, s); break;
+    case 4: gate_regs<1, 2>(a, cm1, s); break;
+    case 5: gate_regs<1, 3>(a, cm1, s); break;
+    case 6: gate_regs<1, 4>(a, cm1, s); break;
+    case 7: gate_regs<2, 3>(a, cm1, s); break;
+    case 8: gate_regs<2, 4>(a, cm1, s); break;
+    default: gate_regs<3, 4>(a, cm1, s); break;
+  }
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+}  // namespace sw2
+
+__global__ void __launch_bounds__(512)
+sweep2_kernel(float2 *__restrict__ psi, const PassDesc *__restrict__ pdesc,
+              const PhaseDesc *__restrict__ phases, const ROp *__restrict__ rops,
+              const GateCoef *__restrict__ coefs, const uint64_t *__restrict__ qdiag, int M,
+              double2 *partials, unsigned *ticket, double *series, int64_t slot) {
+  extern __shared__ __align__(16) float2 tile2[];
+  __shared__ PassDesc d;
+  __shared__ uint64_t sH[kMaxK];
+  __shared__ uint64_t sQ[kMaxK * kMaxK];
+  __shared__ uint64_t sOut;
+  __shared__ uint64_t s_off_hi[64];   // physical offset of the high chunk-index bits
+  __shared__ uint32_t s_perm_hi[64];  // input tile index of the high output chunk-index bits
+  {
+    const int nwords = (int)(sizeof(PassDesc) / 4);
+    for (int w = threadIdx.x; w < nwords; w += blockDim.x)
+      reinterpret_cast<int *>(&d)[w] = reinterpret_cast<const int *>(pdesc)[w];
+  }
+  __syncthreads();
+  const int K = d.K, tid = threadIdx.x, nt = blockDim.x;
+  const int lognt = 31 - __clz(nt);
+  const uint32_t T = 1u << K;
+  const uint64_t base = deposit_bits(blockIdx.x, d.outer_pos, M - K);
+  // chunks of two amplitudes (tile bit 0): chunk ch = tid + nt * e covers tile
+  // index 2*ch; tile bits 1..lognt come from tid, the rest from e
+  const int ehi = K - 1 - lognt;  // number of high chunk bits
+  for (int e = tid; e < (1 << ehi); e += nt) {
+    uint64_t o = 0;
+    uint32_t pin = 0;
+    for (int k = 0; k < ehi; ++k) {
+      const int q = 1 + lognt + k;
+      if ((e >> k) & 1) o |= 1ull << d.tile_pos[q], pin |= 1u << d.perm[q];
+    }
+    s_off_hi[e] = o;
+    s_perm_hi[e] = pin;
+  }
+  uint64_t off_lo = 0;
+  uint32_t pin_lo = 0;
+  for (int k = 0; k < lognt; ++k)
+    if ((tid >> k) & 1) off_lo |= 1ull << d.tile_pos[1 + k], pin_lo |= 1u << d.perm[1 + k];
+  __syncthreads();
+
+  // ---- global -> shared (16-byte async copies)
+  for (int e = 0; e < (1 << ehi); ++e) {
+    const uint32_t t = ((uint32_t)e << (lognt + 1)) | ((uint32_t)tid << 1);
+    sw2::cp_async16(&tile2[sw2::slot(t)], psi + base + off_lo + s_off_hi[e]);
+  }
+  sw2::cp_async_wait_all();
+  __syncthreads();
+
+  float up = 0.f, dn = 0.f;
+  const int nout = M - K;
+  for (int p = 0; p < d.nphases; ++p) {
+    const PhaseDesc ph = phases[d.phase0 + p];
+    // tile index of this thread's subcube origin and register-bit masks
+    uint32_t t0 = 0;
+    for (int k = 0; k < 5; ++k) t0 |= ((uint32_t)(tid >> k) & 1u) << ph.lanes[k];
+    for (int k = 0; k < K - 10; ++k) t0 |= ((uint32_t)(tid >> (5 + k)) & 1u) << ph.warps[k];
+    uint32_t m[5], sm[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) m[k] = 1u << ph.rb[k], sm[k] = sw2::slot(m[k]);
+    const uint32_t s0 = sw2::slot(t0);
+    if (ph.nops == 1 && rops[ph.op0].kind == OP_DIAG) {
+      // diagonal phase e^{-i tau D}, amplitude by amplitude in shared memory:
+      // Theta(x) = sum_{p<p'} q_pp' sigma_p sigma_p' (mod 2^64) split into
+      // outer-outer (sOut), outer-tile (sH) and tile-tile (sQ) parts
+      const uint64_t *q = qdiag + (size_t)rops[ph.op0].arg * M * M;
+      if (tid < K) {
+        const int pp = d.tile_pos[tid];
+        uint64_t h = 0;
+        for (int o = 0; o < nout; ++o) {
+          const int po = d.outer_pos[o];
+          const uint64_t v = q[pp * M + po];
+          h += ((base >> po) & 1ull) ? v : (0ull - v);
+        }
+        sH[tid] = h;
+      } else if (tid == K) {
+        uint64_t s = 0;
+        for (int o = 0; o < nout; ++o)
+          for (int o2 = o + 1; o2 < nout; ++o2) {
+            const int pa = d.outer_pos[o], pb = d.outer_pos[o2];
+            const uint64_t v = q[pa * M + pb];
+            s += (((base >> pa) ^ (base >> pb)) & 1ull) ? (0ull - v) : v;
+          }
+        sOut = s;
+      }
+      for (int w = tid; w < K * K; w += nt) sQ[w] = q[d.tile_pos[w / K] * M + d.tile_pos[w % K]];
+      __syncthreads();
+      uint32_t isreg = 0;
+      for (int k = 0; k < 5; ++k) isreg |= m[k];
+      // fixed part (tile bits from the thread index) once per thread
+      uint64_t th0 = sOut;
+      for (int x = 0; x < K; ++x) {
+        if ((isreg >> x) & 1u) continue;
+        const uint32_t bx = (t0 >> x) & 1u;
+        th0 += bx ? sH[x] : (0ull - sH[x]);
+        for (int y = x + 1; y < K; ++y) {
+          if ((isreg >> y) & 1u) continue;
+          th0 += (bx ^ ((t0 >> y) & 1u)) ? (0ull - sQ[x * K + y]) : sQ[x * K + y];
+        }
+      }
+      // field on each register bit from the fixed bits, once per thread
+      uint64_t G[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const int rk = ph.rb[k];
+        uint64_t g = sH[rk];
+        for (int x = 0; x < K; ++x) {
+          if ((isreg >> x) & 1u) continue;
+          g += ((t0 >> x) & 1u) ? sQ[x * K + rk] : (0ull - sQ[x * K + rk]);
+        }
+        G[k] = g;
+      }
+      for (int i = 0; i < 32; ++i) {
+        uint32_t s = s0;
+        uint64_t th = th0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          const uint32_t bk = (i >> k) & 1;
+          if (bk) s ^= sm[k];
+          th += bk ? G[k] : (0ull - G[k]);
+#pragma unroll
+          for (int l = k + 1; l < 5; ++l) {
+            const uint64_t v = sQ[ph.rb[k] * K + ph.rb[l]];
+            th += (bk ^ ((i >> l) & 1)) ? (0ull - v) : v;
+          }
+        }
+        tile2[s] = cmul(tile2[s], cis_turns(th, 0.0f));
+      }
+      __syncthreads();
+      continue;
+    }
+    float2 a[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      uint32_t s = s0;
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+        if ((i >> k) & 1) s ^= sm[k];
+      a[i] = tile2[s];
+    }
+    for (int k = 0; k < ph.nops; ++k) {
+      const ROp op = rops[ph.op0 + k];
+      if (op.kind == OP_GATE) {
+        const GateCoef g = coefs[op.coef];
+        sw2::gate_combo(a, op.combo, g.cm1f, g.sf);
+      } else if (op.kind == OP_REDUCE) {
+        int kr = -1;
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+          if (ph.rb[q] == d.site_tile) kr = q;
+        const uint32_t fixed_bit = d.site_tile >= 0 ? ((t0 >> d.site_tile) & 1u)
+                                                    : (uint32_t)((base >> d.site_pos) & 1ull);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float pr = a[i].x * a[i].x + a[i].y * a[i].y;
+          const uint32_t bit = kr >= 0 ? ((uint32_t)(i >> kr) & 1u) : fixed_bit;
+          if (bit) up += pr;
+          else dn += pr;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      uint32_t s = s0;
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+        if ((i >> k) & 1) s ^= sm[k];
+      tile2[s] = a[i];
+    }
+    __syncthreads();
+  }
+
+  // ---- shared -> global, output tile bits relabelled by perm
+  for (int e = 0; e < (1 << ehi); ++e) {
+    const uint32_t tin = pin_lo | s_perm_hi[e];  // input index of output chunk (tile bit 0 = 0)
+    const float2 v0 = tile2[sw2::slot(tin)];
+    const float2 v1 = tile2[sw2::slot(tin | (1u << d.perm[0]))];
+    float4 *dst = reinterpret_cast<float4 *>(psi + base + off_lo + s_off_hi[e]);
+    *dst = make_float4(v0.x, v0.y, v1.x, v1.y);
+  }
+  if (d.has_reduce) reduce_finalize((double)up, (double)dn, partials, ticket, series, slot);
+}
+
+}  // namespace spinrp

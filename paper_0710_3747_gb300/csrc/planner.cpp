@@ -1,0 +1,227 @@
+// planner.cpp -- cuts the forward half step of the Trotter product into
+// shared-memory tile sweeps.
+//
+// The forward half step applies the flip-flop bonds in canonical order
+// g_0, g_1, ..., g_{B-1}.  Two gates on disjoint spin pairs commute exactly, so
+// any order that keeps, for every spin, the sequence of gates touching it is
+// the same operator.  The planner exploits this freedom (and nothing else): it
+// greedily grows a set Q of K spins and takes every gate that becomes
+// applicable using spins of Q only; that set of gates is one segment (one
+// device sweep over 2^(M-K) tiles of 2^K amplitudes).  It repeats until every
+// gate is placed.  The reverse half step reuses the segments backwards.
+//
+// Coalescing: every tile must contain the c lowest physical bits, so that a
+// tile is made of contiguous runs of 2^c amplitudes.  Consecutive segments k,
+// k+1 therefore share c spins X_k ("exit set" of k): sweep k writes its tile
+// back with X_k moved into the low bits (an in-place relabelling of bit
+// positions inside the tile), and segment k+1 is grown starting from X_k.
+// On the way back (reverse half step) each sweep undoes its relabelling, so
+// the layout at every step boundary is the same (pos).
+#include <algorithm>
+#include <limits>
+#include <queue>
+
+#include "internal.h"
+
+namespace spinrp {
+
+namespace {
+
+struct Frontier {
+  const std::vector<std::pair<int, int>> *bonds;
+  const std::vector<std::vector<int>> *chain;  // per spin: bonds touching it, in order
+  std::vector<int> ptr;                        // per spin: next undone position in its chain
+  int ndone = 0;
+
+  bool ready(int b) const {
+    const auto &bd = (*bonds)[b];
+    const auto &ci = (*chain)[bd.first], &cj = (*chain)[bd.second];
+    return ptr[bd.first] < (int)ci.size() && ci[ptr[bd.first]] == b &&
+           ptr[bd.second] < (int)cj.size() && cj[ptr[bd.second]] == b;
+  }
+  int head(int q) const {
+    const auto &c = (*chain)[q];
+    return ptr[q] < (int)c.size() ? c[ptr[q]] : -1;
+  }
+  int pending(int q) const { return (int)(*chain)[q].size() - ptr[q]; }
+  // Apply every gate reachable inside spin set Q (bit mask), smallest bond
+  // index first; appends the applied bonds to out (if non-null).
+  int closure(uint64_t Q, std::vector<int> *out) {
+    std::priority_queue<int, std::vector<int>, std::greater<int>> pq;
+    const int M = (int)ptr.size();
+    for (int q = 0; q < M; ++q) {
+      if (!((Q >> q) & 1)) continue;
+      int b = head(q);
+      if (b < 0) continue;
+      const auto &bd = (*bonds)[b];
+      if (((Q >> bd.first) & 1) && ((Q >> bd.second) & 1) && ready(b)) pq.push(b);
+    }
+    int applied = 0, last = -1;
+    while (!pq.empty()) {
+      int b = pq.top();
+      pq.pop();
+      if (b == last || !ready(b)) continue;  // pushed once per endpoint
+      last = b;
+      const auto &bd = (*bonds)[b];
+      ++ptr[bd.first];
+      ++ptr[bd.second];
+      ++applied;
+      ++ndone;
+      if (out) out->push_back(b);
+      for (int q : {bd.first, bd.second}) {
+        int nb = head(q);
+        if (nb < 0) continue;
+        const auto &nbd = (*bonds)[nb];
+        if (((Q >> nbd.first) & 1) && ((Q >> nbd.second) & 1) && ready(nb)) pq.push(nb);
+      }
+    }
+    return applied;
+  }
+};
+
+}  // namespace
+
+bool build_plan(int M, const std::vector<std::pair<int, int>> &bonds, int K, int c, Plan *plan,
+                std::string *err) {
+  if (M < 1 || M > kMaxM || K < 1) {
+    *err = "plan: bad size";
+    return false;
+  }
+  const int B = (int)bonds.size();
+  plan->M = M;
+  plan->seg.clear();
+  plan->segQ.clear();
+  plan->exitX.clear();
+  plan->pos.assign(M, -1);
+  if (K >= M) {
+    // one tile holds the whole state: one segment, canonical order, identity layout
+    plan->K = M;
+    plan->c = M;
+    std::vector<PlanGate> g;
+    for (int b = 0; b < B; ++b) g.push_back({b, bonds[b].first, bonds[b].second});
+    plan->seg.push_back(g);
+    std::vector<int> all(M);
+    for (int q = 0; q < M; ++q) all[q] = q, plan->pos[q] = q;
+    plan->segQ.push_back(all);
+    return true;
+  }
+  c = std::max(0, std::min(c, K - 2));
+  plan->K = K;
+  plan->c = c;
+
+  std::vector<std::vector<int>> chain(M);
+  for (int b = 0; b < B; ++b) {
+    chain[bonds[b].first].push_back(b);
+    chain[bonds[b].second].push_back(b);
+  }
+  Frontier fr;
+  fr.bonds = &bonds;
+  fr.chain = &chain;
+  fr.ptr.assign(M, 0);
+
+  std::vector<int> order;  // spins in order of first use (physical layout)
+  uint64_t placed = 0;
+  auto place = [&](int q) {
+    if (!((placed >> q) & 1)) order.push_back(q), placed |= 1ull << q;
+  };
+
+  uint64_t entry = 0;  // spins the next segment must contain (previous exit set)
+  int guard = 0;
+  while (fr.ndone < B || plan->seg.empty()) {
+    if (++guard > 4 * B + 8) {
+      *err = "plan: no progress (tile too narrow)";
+      return false;
+    }
+    uint64_t Q = entry;
+    std::vector<int> added;
+    while (__builtin_popcountll(Q) < K) {
+      Frontier base_trial = fr;
+      const long base = base_trial.closure(Q, nullptr);
+      int best = -1;
+      long best_gain = -1, best_adj = -1, best_first = std::numeric_limits<long>::min();
+      for (int q = 0; q < M; ++q) {
+        if ((Q >> q) & 1) continue;
+        Frontier trial = fr;
+        const long gain = trial.closure(Q | (1ull << q), nullptr);
+        long adj = 0, first = B;
+        for (int k = fr.ptr[q]; k < (int)chain[q].size(); ++k) {
+          const int b = chain[q][k];
+          const int other = bonds[b].first == q ? bonds[b].second : bonds[b].first;
+          if ((Q >> other) & 1) ++adj;
+          first = std::min<long>(first, b);
+        }
+        const bool better = best < 0 || gain > best_gain || (gain == best_gain && adj > best_adj) ||
+                            (gain == best_gain && adj == best_adj && -first > best_first);
+        if (better) best = q, best_gain = gain, best_adj = adj, best_first = -first;
+      }
+      if (best < 0) break;
+      if (best_gain <= base) {
+        // no single spin adds a gate: take the spins of the earliest gate that
+        // is ready after the closure of Q and fits (the smallest undone gate is
+        // always ready, so with K >= c + 2 this always makes progress)
+        Frontier after = fr;
+        after.closure(Q, nullptr);
+        const int room = K - __builtin_popcountll(Q);
+        int pick = -1;
+        for (int b = 0; b < B && pick < 0; ++b) {
+          if (!after.ready(b)) continue;
+          const int need = !((Q >> bonds[b].first) & 1) + !((Q >> bonds[b].second) & 1);
+          if (need > 0 && need <= room) pick = b;
+        }
+        if (pick < 0) break;
+        for (int q : {bonds[pick].first, bonds[pick].second})
+          if (!((Q >> q) & 1)) Q |= 1ull << q, added.push_back(q);
+        continue;
+      }
+      Q |= 1ull << best;
+      added.push_back(best);
+    }
+    // a tile always spans exactly K spins: pad with unused ones
+    for (int q = 0; q < M && __builtin_popcountll(Q) < K; ++q)
+      if (!((Q >> q) & 1)) Q |= 1ull << q, added.push_back(q);
+    std::vector<int> applied;
+    fr.closure(Q, &applied);
+    if (applied.empty() && fr.ndone < B) {
+      *err = "plan: a segment placed no gate (tile too narrow)";
+      return false;
+    }
+    std::vector<PlanGate> g;
+    for (int b : applied) g.push_back({b, bonds[b].first, bonds[b].second});
+    plan->seg.push_back(g);
+    std::vector<int> qs;
+    for (int q = 0; q < M; ++q)
+      if ((Q >> q) & 1) qs.push_back(q);
+    plan->segQ.push_back(qs);
+    // exit set: the c spins of Q whose next pending gate comes earliest
+    std::vector<std::pair<long, int>> cand;
+    for (int q : qs) {
+      const int h = fr.head(q);
+      cand.push_back({h < 0 ? (long)B + 1000 - fr.pending(q) : (long)h, q});
+    }
+    std::sort(cand.begin(), cand.end());
+    std::vector<int> X;
+    for (int k = 0; k < c; ++k) X.push_back(cand[k].second);
+    std::sort(X.begin(), X.end());
+    plan->exitX.push_back(X);
+    entry = 0;
+    for (int q : X) entry |= 1ull << q;
+    for (int q : added) place(q);
+  }
+  const int s = (int)plan->seg.size();
+  // layout at step boundaries: the first exit set in the low bits (for a
+  // single segment: the first c spins of its tile), then spins in order of use
+  std::vector<int> low = s >= 2 ? plan->exitX[0]
+                                : std::vector<int>(plan->segQ[0].begin(), plan->segQ[0].begin() + c);
+  std::vector<int> final_order = low;
+  uint64_t in_low = 0;
+  for (int q : low) in_low |= 1ull << q;
+  for (int q : order)
+    if (!((in_low >> q) & 1)) final_order.push_back(q);
+  for (int q = 0; q < M; ++q)
+    if (!((placed >> q) & 1) && !((in_low >> q) & 1)) final_order.push_back(q);
+  for (int p = 0; p < M; ++p) plan->pos[final_order[p]] = p;
+  plan->exitX.resize(std::max(0, s - 1));
+  return true;
+}
+
+}  // namespace spinrp

@@ -1,0 +1,306 @@
+"""Python binding of the C ABI in ``include/spinrp.h`` (ctypes).
+
+Argument marshalling only: every step of the path runs in ``libspinrp.so``.
+Function names mirror the C entry points without their ``spinrp_`` prefix;
+``System`` and ``State`` wrap the handles.  Device buffers of a state are
+allocated with PyTorch's caching allocator (``torch.empty`` on the current
+CUDA device) and handed to the library as plain pointers; the stream is
+PyTorch's current stream unless one is given.
+
+There is no fallback: if the library is not built, or cannot run, calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from pathlib import Path
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ESTATE = range(7)
+KERNEL_SWEEP, KERNEL_INIT, KERNEL_TABLES = range(3)
+XY, DIPOLAR, ISOTROPIC, ISING, GENERIC = range(5)
+C64, C128 = 0, 1
+_PREC = {"c64": C64, "complex64": C64, "fp32": C64, C64: C64,
+         "c128": C128, "complex128": C128, "fp64": C128, C128: C128}
+
+
+class SpinrpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"spinrp error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> Path:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libspinrp.so (raises if it is not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not path.exists():
+            if build_if_missing:
+                _build.build()
+            else:
+                raise ImportError(f"{path} is not built; run __graft_entry__.build() or "
+                                  f"python -m paper_0710_3747_gb300.build")
+        L = ctypes.CDLL(str(path))
+        vp, i32p, i64p, dp = (ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double))
+        ip, szp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)
+        sig = {
+            "spinrp_last_error": ([], ctypes.c_char_p),
+            "spinrp_version": ([], ctypes.c_char_p),
+            "spinrp_system_create": ([ctypes.c_int, dp, ctypes.c_int, dp, ctypes.POINTER(vp)], ctypes.c_int),
+            "spinrp_system_destroy": ([vp], None),
+            "spinrp_system_num_spins": ([vp], ctypes.c_int),
+            "spinrp_system_bonds": ([vp, i32p, ctypes.c_int, ip], ctypes.c_int),
+            "spinrp_system_set_tile": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "spinrp_system_plan_info": ([vp, ctypes.c_int, ip, ip, ip], ctypes.c_int),
+            "spinrp_system_plan_gates": ([vp, ctypes.c_int, i32p, i32p, ctypes.c_int, ip], ctypes.c_int),
+            "spinrp_state_bytes": ([vp, ctypes.c_int, ctypes.c_int64, szp, szp], ctypes.c_int),
+            "spinrp_state_create": ([vp, ctypes.c_int, vp, ctypes.c_int64, vp, vp, ctypes.POINTER(vp)],
+                                    ctypes.c_int),
+            "spinrp_state_destroy": ([vp], None),
+            "spinrp_state_init_random_phase": ([vp, ctypes.c_uint64], ctypes.c_int),
+            "spinrp_state_load": ([vp, dp], ctypes.c_int),
+            "spinrp_evolve": ([vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
+            "spinrp_series_length": ([vp], ctypes.c_int64),
+            "spinrp_polarization": ([vp, ctypes.c_int, dp, ctypes.c_int64, i64p], ctypes.c_int),
+            "spinrp_norm_series": ([vp, dp, ctypes.c_int64, i64p], ctypes.c_int),
+            "spinrp_state_read": ([vp, i64p, ctypes.c_int64, dp], ctypes.c_int),
+            "spinrp_state_layout": ([vp, i32p, ctypes.POINTER(vp)], ctypes.c_int),
+            "spinrp_profile": ([vp, ctypes.c_int], ctypes.c_int),
+            "spinrp_profile_read": ([vp, ctypes.c_int, dp, i64p], ctypes.c_int),
+            "spinrp_launch_count": ([], ctypes.c_int64),
+            "spinrp_state_transfer_bytes": ([vp, i64p, i64p], ctypes.c_int),
+            "spinrp_system_plan_check": ([vp, ctypes.c_int, dp, dp], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise SpinrpError(rc, lib().spinrp_last_error().decode())
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def version() -> str:
+    return lib().spinrp_version().decode()
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib().spinrp_launch_count())
+
+
+# ---------------------------------------------------------------------------
+# systems
+# ---------------------------------------------------------------------------
+def system_create(J, htype: int, a_generic=None) -> ctypes.c_void_p:
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    M = J.shape[0]
+    a = None if a_generic is None else np.ascontiguousarray(a_generic, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(lib().spinrp_system_create(M, _dp(J), int(htype), None if a is None else _dp(a),
+                                      ctypes.byref(h)))
+    return h
+
+
+class System:
+    """A spin system (couplings + sweep plan), host side."""
+
+    def __init__(self, J, htype: int, a_generic=None):
+        self._h = system_create(J, htype, a_generic)
+        self.J = np.array(J, dtype=np.float64)
+        self.htype = int(htype)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def M(self) -> int:
+        return lib().spinrp_system_num_spins(self._h)
+
+    def bonds(self) -> list[tuple[int, int]]:
+        n = ctypes.c_int()
+        _check(lib().spinrp_system_bonds(self._h, None, 0, ctypes.byref(n)))
+        buf = (ctypes.c_int32 * (2 * max(n.value, 1)))()
+        _check(lib().spinrp_system_bonds(self._h, buf, n.value, ctypes.byref(n)))
+        return [(buf[2 * k], buf[2 * k + 1]) for k in range(n.value)]
+
+    def set_tile(self, prec, K: int):
+        _check(lib().spinrp_system_set_tile(self._h, _PREC[prec], int(K)))
+
+    def plan_info(self, prec="c64") -> dict:
+        s, w, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().spinrp_system_plan_info(self._h, _PREC[prec], ctypes.byref(s), ctypes.byref(w),
+                                             ctypes.byref(k)))
+        return {"segments": s.value, "sweeps_per_step": w.value, "K": k.value}
+
+    def plan_gates(self, prec="c64"):
+        n = ctypes.c_int()
+        _check(lib().spinrp_system_plan_gates(self._h, _PREC[prec], None, None, 0, ctypes.byref(n)))
+        m = max(n.value, 1)
+        pairs, seg = (ctypes.c_int32 * (2 * m))(), (ctypes.c_int32 * m)()
+        _check(lib().spinrp_system_plan_gates(self._h, _PREC[prec], pairs, seg, n.value, ctypes.byref(n)))
+        return [((pairs[2 * k], pairs[2 * k + 1]), seg[k]) for k in range(n.value)]
+
+    def plan_check(self, prec="c64") -> dict:
+        """Host self-check of the device program; raises on a mismatch."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(lib().spinrp_system_plan_check(self._h, _PREC[prec], ctypes.byref(a), ctypes.byref(b)))
+        return {"phases_per_sweep": a.value, "gates_per_phase": b.value}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.spinrp_system_destroy(h)
+            self._h = None
+
+
+def state_bytes(system: System, prec, series_cap: int) -> tuple[int, int]:
+    p, w = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().spinrp_state_bytes(system.handle, _PREC[prec], int(series_cap), ctypes.byref(p),
+                                    ctypes.byref(w)))
+    return p.value, w.value
+
+
+class State:
+    """One device-resident state and its FP64 P(t)/norm series.
+
+    Device memory comes from PyTorch (``alloc="torch"``, default) or from the
+    library's own cudaMalloc (``alloc="library"``)."""
+
+    def __init__(self, system: System, prec="c64", series_cap: int = 1024, stream=None,
+                 alloc: str = "torch"):
+        self.system = system
+        self.prec = _PREC[prec]
+        self.M = system.M
+        psi_b, work_b = state_bytes(system, self.prec, series_cap)
+        self._bufs = []
+        psi_ptr = work_ptr = None
+        if stream is None or alloc == "torch":
+            import torch
+            if not torch.cuda.is_available():
+                raise SpinrpError(ECUDA, "no CUDA device available")
+            if stream is None:
+                stream = torch.cuda.current_stream().cuda_stream
+            if alloc == "torch":
+                psi = torch.empty(psi_b, dtype=torch.uint8, device="cuda")
+                work = torch.empty(work_b, dtype=torch.uint8, device="cuda")
+                self._bufs = [psi, work]
+                psi_ptr, work_ptr = psi.data_ptr(), work.data_ptr()
+        self.stream = int(stream) if stream is not None else 0
+        h = ctypes.c_void_p()
+        _check(lib().spinrp_state_create(system.handle, self.prec, ctypes.c_void_p(self.stream),
+                                         int(series_cap), ctypes.c_void_p(psi_ptr),
+                                         ctypes.c_void_p(work_ptr), ctypes.byref(h)))
+        self._h = h
+        self.psi_bytes, self.work_bytes = psi_b, work_b
+
+    @property
+    def handle(self):
+        return self._h
+
+    def init_random_phase(self, seed: int):
+        _check(lib().spinrp_state_init_random_phase(self._h, int(seed) & (2**64 - 1)))
+        return self
+
+    def load(self, amps: np.ndarray):
+        a = np.ascontiguousarray(np.asarray(amps, dtype=np.complex128)).view(np.float64)
+        assert a.size == 2 << self.M
+        _check(lib().spinrp_state_load(self._h, _dp(a)))
+        return self
+
+    def evolve(self, dt: float, steps: int, order: int = 2):
+        _check(lib().spinrp_evolve(self._h, float(dt), int(steps), int(order)))
+        return self
+
+    def series_length(self) -> int:
+        return int(lib().spinrp_series_length(self._h))
+
+    def polarization(self, site: int = 1) -> np.ndarray:
+        n = self.series_length()
+        out = np.empty(max(n, 1), dtype=np.float64)
+        got = ctypes.c_int64()
+        _check(lib().spinrp_polarization(self._h, int(site), _dp(out), n, ctypes.byref(got)))
+        return out[:got.value]
+
+    def norm_series(self) -> np.ndarray:
+        n = self.series_length()
+        out = np.empty(max(n, 1), dtype=np.float64)
+        got = ctypes.c_int64()
+        _check(lib().spinrp_norm_series(self._h, _dp(out), n, ctypes.byref(got)))
+        return out[:got.value]
+
+    def read(self, idx) -> np.ndarray:
+        idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+        out = np.empty(2 * idx.size, dtype=np.float64)
+        _check(lib().spinrp_state_read(self._h, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                       idx.size, _dp(out)))
+        return out.view(np.complex128)
+
+    def amplitudes(self) -> np.ndarray:
+        """All 2^M amplitudes in logical order (complex128)."""
+        return self.read(np.arange(1 << self.M, dtype=np.int64))
+
+    def layout(self) -> list[int]:
+        lay = (ctypes.c_int32 * self.M)()
+        p = ctypes.c_void_p()
+        _check(lib().spinrp_state_layout(self._h, lay, ctypes.byref(p)))
+        return list(lay)
+
+    def profile(self, enable: bool = True):
+        _check(lib().spinrp_profile(self._h, int(bool(enable))))
+
+    def profile_read(self, kind: int = KERNEL_SWEEP) -> tuple[float, int]:
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _check(lib().spinrp_profile_read(self._h, int(kind), ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def transfer_bytes(self) -> tuple[int, int]:
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().spinrp_state_transfer_bytes(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.spinrp_state_destroy(h)
+        self._h = None
+        self._bufs = []
+
+    def __del__(self):
+        self.close()
+
+
+def run_job(J, htype: int, seed: int, dt: float, steps: int, prec="c64", a_generic=None,
+            tile_K: int | None = None):
+    """Whole job through the C ABI: returns (P[0..steps], norm[0..steps], state)."""
+    sysm = System(J, htype, a_generic)
+    if tile_K:
+        sysm.set_tile(prec, tile_K)
+    st = State(sysm, prec, series_cap=steps + 1)
+    st.init_random_phase(seed).evolve(dt, steps)
+    return st.polarization(1), st.norm_series(), st

@@ -1,0 +1,169 @@
+"""Host-side tests of the C-ABI library (no GPU needed).
+
+* the library loads and exports every entry point that include/spinrp.h declares;
+* spin systems: Hamiltonian families, canonical bond order (checked against
+  the oracle's definition), argument validation;
+* the sweep plan: the device gate order is the canonical one up to exchanges
+  of gates on disjoint spins (per-spin gate sequences identical), every gate
+  appears exactly once, and the sweep counts are as designed.
+"""
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0710_3747_gb300 import build, spinrp
+from paper_0710_3747_gb300 import workloads as W
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def _declared_symbols():
+    text = (ROOT / "include" / "spinrp.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(spinrp_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = spinrp.lib()
+    syms = _declared_symbols()
+    assert len(syms) >= 20
+    for s in syms:
+        assert hasattr(L, s), s
+    assert "sm_103a" in spinrp.version()
+
+
+def _systems():
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=(9, 9))
+    A = A + A.T
+    return [
+        ("ladder14", W.ladder(7, 1.0, 0.5), spinrp.XY, None),
+        ("ladder30", W.ladder(15, 1.0, 0.5), spinrp.XY, None),
+        ("star20", W.star_dipolar(20, 2), spinrp.DIPOLAR, None),
+        ("star22", W.star_dipolar(22, 9), spinrp.DIPOLAR, None),
+        ("iso9", W.star_gaussian(9, 1), spinrp.ISOTROPIC, None),
+        ("generic9", W.star_gaussian(9, 2), spinrp.GENERIC, A),
+        ("chain24", W.chain(24, 1.0), spinrp.XY, None),
+    ]
+
+
+@pytest.mark.parametrize("name,J,htype,a", _systems(), ids=lambda v: v if isinstance(v, str) else "")
+def test_bonds_are_canonical(name, J, htype, a):
+    s = spinrp.System(J, htype, a)
+    _, b = oracle.couplings(J, htype, a)
+    want = [(i + 1, j + 1) for i, j in oracle.canonical_bonds(b)]
+    assert s.bonds() == want
+
+
+def _chains(gates, M):
+    ch = [[] for _ in range(M + 1)]
+    for i, j in gates:
+        ch[i].append((i, j))
+        ch[j].append((i, j))
+    return ch
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("name,J,htype,a", _systems(), ids=lambda v: v if isinstance(v, str) else "")
+def test_plan_is_canonical_up_to_disjoint_exchanges(name, J, htype, a, prec):
+    s = spinrp.System(J, htype, a)
+    M = s.M
+    canon = s.bonds()
+    plan = s.plan_gates(prec)
+    gates = [g for g, _ in plan]
+    segs = [k for _, k in plan]
+    assert sorted(gates) == sorted(canon)           # each gate exactly once
+    assert _chains(gates, M) == _chains(canon, M)   # same order on every spin
+    assert segs == sorted(segs)                     # segments in sweep order
+    info = s.plan_info(prec)
+    assert info["segments"] == max(segs) + 1
+    if M <= info["K"]:
+        assert info["segments"] == 1 and info["sweeps_per_step"] == 1
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("K", list(range(2, 14)))
+@pytest.mark.parametrize("kind", ["star16", "ladder12", "chain13", "generic11"])
+def test_plan_every_tile_width(kind, K, prec):
+    rng = np.random.default_rng(7)
+    J, ht = {"star16": (W.star_dipolar(16, 5), spinrp.DIPOLAR),
+             "ladder12": (W.ladder(6, 1.0, 0.5), spinrp.XY),
+             "chain13": (W.chain(13), spinrp.XY),
+             "generic11": (W.star_gaussian(11, 3), spinrp.ISOTROPIC)}[kind]
+    s = spinrp.System(J, ht)
+    s.set_tile(prec, K)
+    info = s.plan_info(prec)
+    assert info["K"] == min(K, s.M)
+    gates = [g for g, _ in s.plan_gates(prec)]
+    assert sorted(gates) == sorted(s.bonds())
+    assert _chains(gates, s.M) == _chains(s.bonds(), s.M)
+    spinrp.state_bytes(s, prec, 4)  # the sweep descriptors validate too
+
+
+@pytest.mark.parametrize("K", [10, 11, 12, 13, 14])
+@pytest.mark.parametrize("name,J,htype,a", _systems(), ids=lambda v: v if isinstance(v, str) else "")
+def test_register_phase_programs(name, J, htype, a, K):
+    """Every sweep's register-blocked program, run on a random host tile,
+    equals the sweep's plain op list (gates, diagonal phase, reduction)."""
+    s = spinrp.System(J, htype, a)
+    s.set_tile("c64", K)
+    st = s.plan_check("c64")
+    if s.M >= 10:
+        assert st["phases_per_sweep"] >= 1.0
+        if s.bonds():
+            assert 1.0 <= st["gates_per_phase"] <= 10.0
+
+
+def test_plan_sweep_counts():
+    # 2x15 ladder, 14-spin tiles sharing 4 low bits: three segments -> four sweeps per step
+    s = spinrp.System(W.ladder(15, 1.0, 0.5), spinrp.XY)
+    assert s.plan_info("c64") == {"segments": 3, "sweeps_per_step": 4, "K": 14}
+    # M=20 dipolar star, 14-spin tiles: three segments
+    s = spinrp.System(W.star_dipolar(20, 2), spinrp.DIPOLAR)
+    assert s.plan_info("c64")["segments"] <= 3
+
+
+def test_state_bytes():
+    s = spinrp.System(W.ladder(7, 1.0, 0.5), spinrp.XY)
+    p64, w64 = spinrp.state_bytes(s, "c64", 401)
+    p128, _ = spinrp.state_bytes(s, "c128", 401)
+    assert p64 == 8 << 14 and p128 == 16 << 14
+    assert w64 >= 16 * 401
+
+
+@pytest.mark.parametrize("bad", [
+    dict(J=np.zeros((1, 1)), htype=spinrp.XY),
+    dict(J=np.zeros((35, 35)), htype=spinrp.XY),
+    dict(J=np.zeros((4, 4)), htype=9),
+    dict(J=np.zeros((4, 4)), htype=spinrp.GENERIC),
+    dict(J=np.full((4, 4), np.nan), htype=spinrp.XY),
+])
+def test_system_create_rejects(bad):
+    with pytest.raises(spinrp.SpinrpError) as e:
+        spinrp.System(bad["J"], bad["htype"])
+    assert e.value.code == spinrp.EINVAL
+
+
+def test_set_tile_rejects():
+    s = spinrp.System(W.ladder(3), spinrp.XY)
+    with pytest.raises(spinrp.SpinrpError):
+        s.set_tile("c64", 15)
+    with pytest.raises(spinrp.SpinrpError):
+        s.set_tile("c128", 14)
+
+
+def test_hamiltonian_families_match_oracle_convention():
+    # the library's (a, b) for each family reproduces the oracle's through the
+    # bond list (b != 0 pattern) -- dipolar b = -J keeps every pair
+    J = W.star_dipolar(6, 1)
+    for ht in (spinrp.XY, spinrp.DIPOLAR, spinrp.ISOTROPIC):
+        assert len(spinrp.System(J, ht).bonds()) == 15
+    assert spinrp.System(J, spinrp.ISING).bonds() == []

@@ -1,0 +1,266 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (stated by the task for P(t)): |dP| <= 1e-10 for the FP64 path and
+|dP| <= 1e-4 for the FP32 path, at every recorded step.  Amplitudes of the
+FP64 path are compared at 1e-11 (a few hundred gate applications of FP64
+rounding); the FP32 initial state at 2e-7 relative (FP32 rounding of the
+phase).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0710_3747_gb300 import spinrp
+from paper_0710_3747_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+THREADS = os.cpu_count() or 1
+TOL_P = {"c128": 1e-10, "c64": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    spinrp.lib()
+
+
+def _oracle(J, htype, seed, dt, steps, a=None):
+    return oracle.run(J, htype, seed, dt, steps, a_generic=a, threads=THREADS)
+
+
+def _gpu(J, htype, seed, dt, steps, prec, a=None, K=None, chunks=None):
+    s = spinrp.System(J, htype, a)
+    if K:
+        s.set_tile(prec, K)
+    st = spinrp.State(s, prec, series_cap=steps + 1)
+    st.init_random_phase(seed)
+    for n in (chunks or [steps]):
+        st.evolve(dt, n)
+    return st.polarization(1), st.norm_series(), st
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("M", [2, 3, 5, 14, 20])
+def test_initial_state(prec, M):
+    J = W.chain(M)
+    s = spinrp.System(J, spinrp.XY)
+    st = spinrp.State(s, prec, series_cap=1)
+    st.init_random_phase(12345 + M)
+    got = st.amplitudes()
+    want = oracle.init_random_phase(M, 12345 + M, threads=THREADS)
+    tol = 1e-15 if prec == "c128" else 2e-7 * 2.0 ** (-(M - 1) / 2)
+    assert np.max(np.abs(got - want)) < tol
+    P, nrm = st.polarization(1), st.norm_series()
+    assert P[0] == pytest.approx(1.0, abs=1e-15)
+    assert nrm[0] == pytest.approx(1.0, abs=1e-13 if prec == "c128" else 1e-6)
+
+
+def _small_systems():
+    rng = np.random.default_rng(5)
+    A = rng.normal(size=(7, 7))
+    A = A + A.T
+    return [
+        ("pair", np.array([[0, 1.3], [1.3, 0]]), spinrp.DIPOLAR, None),
+        ("ladder6", W.ladder(3, 1.0, 0.5), spinrp.XY, None),
+        ("chain9", W.chain(9, 0.8), spinrp.XY, None),
+        ("star8", W.star_dipolar(8, 3), spinrp.DIPOLAR, None),
+        ("iso7", W.star_gaussian(7, 4), spinrp.ISOTROPIC, None),
+        ("ising6", W.star_gaussian(6, 5), spinrp.ISING, None),
+        ("generic7", W.star_gaussian(7, 6), spinrp.GENERIC, A),
+        ("ladder10", W.ladder(5, 1.0, 0.1), spinrp.XY, None),
+    ]
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("name,J,htype,a", _small_systems(), ids=lambda v: v if isinstance(v, str) else "")
+def test_small_systems_full_state(name, J, htype, a, prec):
+    seed, dt, steps = 77, 0.07, 9
+    Pw, Nw, psi_w = _oracle(J, htype, seed, dt, steps, a)
+    Pg, Ng, st = _gpu(J, htype, seed, dt, steps, prec, a)
+    assert np.max(np.abs(Pg - Pw)) <= (1e-12 if prec == "c128" else 1e-5)
+    assert np.max(np.abs(Ng - Nw)) <= (1e-12 if prec == "c128" else 1e-5)
+    amp = st.amplitudes()
+    assert np.max(np.abs(amp - psi_w)) <= (1e-12 if prec == "c128" else 2e-6)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("K", [4, 5, 6, 8, 9])
+@pytest.mark.parametrize("kind", ["star12", "ladder12", "generic11"])
+def test_multi_tile_plans(kind, K, prec):
+    """Narrow tiles force several segments, relabelling sweeps, the diagonal
+    phase split across tile/outer bits and the readout spin in outer bits."""
+    if kind == "star12":
+        J, ht, a = W.star_dipolar(12, 8), spinrp.DIPOLAR, None
+    elif kind == "ladder12":
+        J, ht, a = W.ladder(6, 1.0, 0.5), spinrp.XY, None
+    else:
+        rng = np.random.default_rng(2)
+        a = rng.normal(size=(11, 11)); a = a + a.T
+        J, ht = W.star_gaussian(11, 3), spinrp.GENERIC
+    seed, dt, steps = 5, 0.05, 6
+    Pw, Nw, psi_w = _oracle(J, ht, seed, dt, steps, a)
+    Pg, Ng, st = _gpu(J, ht, seed, dt, steps, prec, a, K=K)
+    info = st.system.plan_info(prec)
+    assert info["K"] == K
+    assert np.max(np.abs(Pg - Pw)) <= (1e-12 if prec == "c128" else 1e-5), info
+    amp = st.amplitudes()
+    assert np.max(np.abs(amp - psi_w)) <= (1e-12 if prec == "c128" else 2e-6), info
+
+
+@pytest.mark.parametrize("K", [10, 11, 12, 13])
+@pytest.mark.parametrize("kind", ["star16", "ladder16", "generic15", "chain18"])
+def test_register_blocked_sweeps(kind, K):
+    """complex64 tiles of K >= 10 spins run the register-blocked sweep:
+    several tiles and segments, relabelling, diagonal phase across tile and
+    outer bits."""
+    rng = np.random.default_rng(4)
+    a = None
+    if kind == "star16":
+        J, ht = W.star_dipolar(16, 8), spinrp.DIPOLAR
+    elif kind == "ladder16":
+        J, ht = W.ladder(8, 1.0, 0.5), spinrp.XY
+    elif kind == "chain18":
+        J, ht = W.chain(18, 0.9), spinrp.XY
+    else:
+        a = rng.normal(size=(15, 15)); a = a + a.T
+        J, ht = W.star_gaussian(15, 3), spinrp.GENERIC
+    seed, dt, steps = 11, 0.04, 5
+    Pw, Nw, psi_w = _oracle(J, ht, seed, dt, steps, a)
+    Pg, Ng, st = _gpu(J, ht, seed, dt, steps, "c64", a, K=K)
+    assert st.system.plan_info("c64")["K"] == K
+    assert np.max(np.abs(Pg - Pw)) <= 1e-5
+    amp = st.amplitudes()
+    assert np.max(np.abs(amp - psi_w)) <= 2e-6 * 2.0 ** (-(st.M - 1) / 2) * 64
+
+
+@pytest.mark.parametrize("steps", [1, 2, 3])
+def test_few_steps_and_chunked_evolve(steps):
+    J = W.star_dipolar(10, 4)
+    Pw, _, psi_w = _oracle(J, spinrp.DIPOLAR, 3, 0.03, 2 * steps)
+    # one call, and the same steps in two calls (D(dt/2) D(dt/2) at the seam)
+    for chunks in ([2 * steps], [steps, steps]):
+        Pg, _, st = _gpu(J, spinrp.DIPOLAR, 3, 0.03, 2 * steps, "c128", K=6, chunks=chunks)
+        assert np.max(np.abs(Pg - Pw)) < 1e-12
+        assert np.max(np.abs(st.amplitudes() - psi_w)) < 1e-12
+
+
+def test_time_reversal_on_gpu():
+    J = W.star_dipolar(12, 6)
+    s = spinrp.System(J, spinrp.DIPOLAR)
+    s.set_tile("c128", 7)
+    st = spinrp.State(s, "c128", series_cap=41)
+    st.init_random_phase(9)
+    psi0 = st.amplitudes()
+    st.evolve(0.05, 20)
+    assert np.max(np.abs(st.amplitudes() - psi0)) > 1e-3
+    st.evolve(-0.05, 20)
+    assert np.max(np.abs(st.amplitudes() - psi0)) < 1e-12
+
+
+def test_load_arbitrary_state():
+    M = 9
+    rng = np.random.default_rng(0)
+    psi = rng.normal(size=1 << M) + 1j * rng.normal(size=1 << M)
+    psi /= np.linalg.norm(psi)
+    J = W.star_dipolar(M, 1)
+    a, b = oracle.couplings(J, oracle.DIPOLAR)
+    ref = psi.copy()
+    P, _ = oracle.evolve(ref, a, b, 0.04, 10)
+    s = spinrp.System(J, spinrp.DIPOLAR)
+    s.set_tile("c128", 5)
+    st = spinrp.State(s, "c128", series_cap=11)
+    st.load(psi)
+    assert st.polarization()[0] == pytest.approx(oracle.polarization(psi), abs=1e-14)
+    st.evolve(0.04, 10)
+    assert np.max(np.abs(st.polarization()[1:] - P)) < 1e-12
+    assert np.max(np.abs(st.amplitudes() - ref)) < 1e-12
+
+
+def test_deterministic_series():
+    J = W.star_dipolar(16, 2)
+    out = [_gpu(J, spinrp.DIPOLAR, 4, 0.02, 30, "c64")[0] for _ in range(2)]
+    assert np.array_equal(out[0], out[1])
+
+
+def test_errors_are_reported():
+    s = spinrp.System(W.ladder(3), spinrp.XY)
+    st = spinrp.State(s, "c64", series_cap=3)
+    with pytest.raises(spinrp.SpinrpError) as e:
+        st.evolve(0.1, 1)
+    assert e.value.code == spinrp.ESTATE
+    st.init_random_phase(1)
+    with pytest.raises(spinrp.SpinrpError) as e:
+        st.evolve(0.1, 5)
+    assert e.value.code == spinrp.EINVAL
+    with pytest.raises(spinrp.SpinrpError) as e:
+        st.evolve(0.1, 1, order=4)
+    assert e.value.code == spinrp.EUNSUPPORTED
+    with pytest.raises(spinrp.SpinrpError) as e:
+        st.polarization(2)
+    assert e.value.code == spinrp.EUNSUPPORTED
+    with pytest.raises(spinrp.SpinrpError):
+        st.evolve(float("nan"), 1)
+    st.evolve(0.1, 2)
+    assert st.series_length() == 3
+
+
+# ---------------------------------------------------------------------------
+# the five workloads
+# ---------------------------------------------------------------------------
+def test_ladder_m14_fp64_and_fp32():
+    """2x7 XY ladder (leg 1, rung 0.5), dt 0.05, 400 steps."""
+    job = W.ladder_m14()
+    Pw, Nw, _ = _oracle(job.J, job.htype, job.seed, job.dt, job.steps)
+    for prec in ("c128", "c64"):
+        Pg, Ng, _ = _gpu(job.J, job.htype, job.seed, job.dt, job.steps, prec)
+        assert Pg.shape == Pw.shape
+        assert np.max(np.abs(Pg - Pw)) <= TOL_P[prec], prec
+    # smaller tiles: several sweeps per step, same operator
+    Pg, _, _ = _gpu(job.J, job.htype, job.seed, job.dt, job.steps, "c128", K=8)
+    assert np.max(np.abs(Pg - Pw)) <= 1e-10
+
+
+def test_star_m20_fp64_and_fp32():
+    """Dipolar star M=20 (19 satellites, rms 1), dt 0.02, 1000 steps."""
+    job = W.star_m20()
+    Pw, Nw, psi_w = _oracle(job.J, job.htype, job.seed, job.dt, job.steps)
+    idx = np.random.default_rng(0).integers(0, 1 << 20, size=4096)
+    for prec in ("c128", "c64"):
+        Pg, Ng, st = _gpu(job.J, job.htype, job.seed, job.dt, job.steps, prec)
+        assert np.max(np.abs(Pg - Pw)) <= TOL_P[prec], prec
+        assert np.max(np.abs(Ng - 1.0)) <= (1e-10 if prec == "c128" else 1e-4)
+        if prec == "c128":
+            assert np.max(np.abs(st.read(idx) - psi_w[idx])) < 1e-10
+
+
+@pytest.mark.slow
+def test_ladder_m30_sampled():
+    """2x15 ladder at full size (2^30 amplitudes, 8 GiB c64 / 16 GiB c128):
+    the first Trotter step against the oracle (P, norm and 2^14 sampled
+    amplitudes) for both precisions, then the invariants over 20 steps."""
+    job = W.ladder_m30()
+    idx = np.random.default_rng(1).integers(0, 1 << 30, size=1 << 14)
+    Pw, Nw, psi_w = _oracle(job.J, job.htype, job.seed, job.dt, 1)
+    ref = psi_w[idx].copy()
+    del psi_w
+    for prec in ("c64", "c128"):
+        st = spinrp.State(spinrp.System(job.J, job.htype), prec, series_cap=32)
+        st.init_random_phase(job.seed)
+        st.evolve(job.dt, 1)
+        got = st.read(idx)
+        Pg = st.polarization()
+        assert np.max(np.abs(Pg - Pw)) <= TOL_P[prec], prec
+        tol = 1e-12 if prec == "c128" else 3e-7 * 2.0 ** -14.5
+        assert np.max(np.abs(got - ref)) < tol, prec
+        st.evolve(job.dt, 19)
+        N = st.norm_series()
+        assert np.max(np.abs(N - 1.0)) < (1e-10 if prec == "c128" else 1e-5)
+        P = st.polarization()
+        assert np.all(np.abs(P) <= 1.0 + 1e-6)
+        st.close()
