@@ -197,6 +197,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     spinrp.lib()
     job, prec, wname = workload(args.workload)
     sysm = spinrp.System(job.J, job.htype)
+    if args.tile_K:
+        sysm.set_tile(prec, args.tile_K)
     nb = len(sysm.bonds())
     info = sysm.plan_info(prec)
     st = spinrp.State(sysm, prec, series_cap=job.steps + 1)
@@ -264,7 +266,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             traffic = None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": "sweep_kernel<float>" if prec == "c64" else "sweep_kernel<double>",
+                "kernel": ("sweep2_kernel" if info["K"] >= 10 else "sweep_kernel<float>") if prec == "c64"
+                else "sweep_kernel<double>",
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
                 "launches": sweep_n, "mean_launch_ms": sweep_avg_s * 1e3,
                 "sweep_share_of_job": sweep_ms / (ms * args.steps)}
@@ -292,6 +295,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if not args.skip_e2e:
         def e2e_job():
             s2 = spinrp.System(job.J, job.htype)
+            if args.tile_K:
+                s2.set_tile(prec, args.tile_K)
             st2 = spinrp.State(s2, prec, series_cap=job.steps + 1)
             st2.init_random_phase(job.seed + rank).evolve(job.dt, job.steps)
             P = st2.polarization()
@@ -358,6 +363,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--cpu-gates", type=int, default=43)
     ap.add_argument("--ref-gates", type=int, default=16)
+    ap.add_argument("--tile-K", type=int, default=0, help="tile width override (autotuner knob)")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")

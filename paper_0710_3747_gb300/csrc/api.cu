@@ -33,12 +33,6 @@ static int fail(int code, const char *fmt, ...) {
   return code;
 }
 
-#define CUDA_TRY(call)                                                                 \
-  do {                                                                                 \
-    cudaError_t e_ = (call);                                                           \
-    if (e_ != cudaSuccess) return fail(SPINRP_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-  } while (0)
-
 static std::atomic<int64_t> g_launches{0};
 
 extern "C" const char *spinrp_last_error(void) { return g_err.c_str(); }
@@ -945,6 +939,74 @@ double check_reduce(const std::vector<cplx> &A) {
   for (size_t t = 0; t < A.size(); ++t) r += std::norm(A[t]) * double(t % 7 + 1);
   return r;
 }
+
+// Host replay of sweep2_kernel's index arithmetic for one pass and one block:
+// global addresses in range (and 16-byte aligned for the vector stores),
+// shared-memory slots in range and each touched exactly once per stage.
+uint32_t host_slot(uint32_t t) { return t ^ (((t >> 4) ^ (t >> 8) ^ (t >> 12)) & 15u); }
+
+std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint64_t block) {
+  const int K = d.K, nt = 1 << (K - 5), lognt = K - 5;
+  const uint32_t T = 1u << K;
+  uint64_t base = 0;
+  for (int k = 0; k < M - K; ++k) base |= ((block >> k) & 1ull) << d.outer_pos[k];
+  auto phys = [&](uint32_t t) {
+    uint64_t o = base;
+    for (int q = 0; q < K; ++q) o |= (uint64_t)((t >> q) & 1u) << d.tile_pos[q];
+    return o;
+  };
+  const uint64_t N = 1ull << M;
+  char buf[160];
+  // load: amplitude t = tid + nt*e
+  std::vector<char> seen(T, 0);
+  for (int tid = 0; tid < nt; ++tid)
+    for (int e = 0; e < (1 << (K - lognt)); ++e) {
+      const uint32_t t = ((uint32_t)e << lognt) | (uint32_t)tid;
+      uint64_t off = 0;
+      for (int k = 0; k < lognt; ++k) if ((tid >> k) & 1) off |= 1ull << d.tile_pos[k];
+      for (int k = 0; k < K - lognt; ++k) if ((e >> k) & 1) off |= 1ull << d.tile_pos[lognt + k];
+      const uint32_t s = host_slot(t);
+      if (t >= T || s >= T || seen[s]++ || base + off >= N || base + off != phys(t)) {
+        snprintf(buf, sizeof buf, "load index out of place (t=%u)", t);
+        return buf;
+      }
+    }
+  // phases: every thread's 32-amplitude subcube, slots by linearity of the swizzle
+  for (int p = 0; p < d.nphases; ++p) {
+    const PhaseDesc &ph = phases[d.phase0 + p];
+    std::fill(seen.begin(), seen.end(), 0);
+    for (int tid = 0; tid < nt; ++tid) {
+      uint32_t t0 = 0;
+      for (int k = 0; k < 5; ++k) t0 |= ((uint32_t)(tid >> k) & 1u) << ph.lanes[k];
+      for (int k = 0; k < K - 10; ++k) t0 |= ((uint32_t)(tid >> (5 + k)) & 1u) << ph.warps[k];
+      for (int i = 0; i < 32; ++i) {
+        uint32_t t = t0, s = host_slot(t0);
+        for (int k = 0; k < 5; ++k)
+          if ((i >> k) & 1) t |= 1u << ph.rb[k], s ^= host_slot(1u << ph.rb[k]);
+        if (t >= T || s != host_slot(t) || s >= T || seen[s]++) {
+          snprintf(buf, sizeof buf, "phase %d subcube index out of place (t=%u)", p, t);
+          return buf;
+        }
+      }
+    }
+  }
+  // store: output chunk 2*(tid + nt*e') of two amplitudes, 16-byte aligned
+  std::fill(seen.begin(), seen.end(), 0);
+  for (int tid = 0; tid < nt; ++tid)
+    for (int e = 0; e < (1 << (K - 1 - lognt)); ++e) {
+      const uint32_t tout = ((uint32_t)e << (lognt + 1)) | ((uint32_t)tid << 1);
+      uint32_t tin = 0;
+      for (int q = 1; q < K; ++q) tin |= ((tout >> q) & 1u) << d.perm[q];
+      const uint32_t tin1 = tin | (1u << d.perm[0]);
+      const uint64_t addr = phys(tout);
+      if ((addr & 1ull) || addr + 1 >= N || tin >= T || tin1 >= T || seen[host_slot(tin)]++ ||
+          seen[host_slot(tin1)]++) {
+        snprintf(buf, sizeof buf, "store index out of place (t=%u)", tout);
+        return buf;
+      }
+    }
+  return "";
+}
 }  // namespace
 
 extern "C" int spinrp_system_plan_check(const spinrp_system *sys, int prec, double *phases_per_sweep,
@@ -966,6 +1028,12 @@ extern "C" int spinrp_system_plan_check(const spinrp_system *sys, int prec, doub
   long nphase = 0, ngate_phase = 0, ngates = 0;
   for (size_t pi = 0; pi < ps.desc.size(); ++pi) {
     const PassDesc &d = ps.desc[pi];
+    const uint64_t nblocks = 1ull << (plan.M - K);
+    for (uint64_t blk : {uint64_t(0), nblocks / 3, nblocks - 1}) {
+      const std::string e = audit_sweep2(d, ps.phases.data(), plan.M, blk);
+      if (!e.empty()) return fail(SPINRP_EINVAL, "plan_check: pass %zu block %llu: %s", pi,
+                                  (unsigned long long)blk, e.c_str());
+    }
     std::vector<cplx> A(T), B;
     for (auto &x : A) x = cplx(nd(rng), nd(rng));
     B = A;

@@ -460,9 +460,11 @@ __device__ __forceinline__ void gate_combo(float2 (&a)[32], int combo, float cm1
   }
 }
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+// 8-byte asynchronous global->shared copy (one amplitude): the swizzle may
+// move an amplitude pair to an odd slot, so 16-byte copies would misalign.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
   const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
@@ -482,6 +484,7 @@ sweep2_kernel(float2 *__restrict__ psi, const PassDesc *__restrict__ pdesc,
   __shared__ uint64_t sOut;
   __shared__ uint64_t s_off_hi[64];   // physical offset of the high chunk-index bits
   __shared__ uint32_t s_perm_hi[64];  // input tile index of the high output chunk-index bits
+  __shared__ uint64_t s_off_amp[32];  // physical offset of the high amplitude-index bits
   {
     const int nwords = (int)(sizeof(PassDesc) / 4);
     for (int w = threadIdx.x; w < nwords; w += blockDim.x)
@@ -509,12 +512,25 @@ sweep2_kernel(float2 *__restrict__ psi, const PassDesc *__restrict__ pdesc,
   uint32_t pin_lo = 0;
   for (int k = 0; k < lognt; ++k)
     if ((tid >> k) & 1) off_lo |= 1ull << d.tile_pos[1 + k], pin_lo |= 1u << d.perm[1 + k];
+  // amplitude a = tid + nt * e: tile bits 0..lognt-1 from tid, the K - lognt
+  // (= 5) high bits from e
+  const int eamp = K - lognt;
+  for (int e = tid; e < (1 << eamp); e += nt) {
+    uint64_t o = 0;
+    for (int k = 0; k < eamp; ++k)
+      if ((e >> k) & 1) o |= 1ull << d.tile_pos[lognt + k];
+    s_off_amp[e] = o;
+  }
+  uint64_t off_amp_lo = 0;
+  for (int k = 0; k < lognt; ++k)
+    if ((tid >> k) & 1) off_amp_lo |= 1ull << d.tile_pos[k];
   __syncthreads();
 
-  // ---- global -> shared (16-byte async copies)
-  for (int e = 0; e < (1 << ehi); ++e) {
-    const uint32_t t = ((uint32_t)e << (lognt + 1)) | ((uint32_t)tid << 1);
-    sw2::cp_async16(&tile2[sw2::slot(t)], psi + base + off_lo + s_off_hi[e]);
+  // ---- global -> shared (8-byte async copies; 16 consecutive threads read
+  // one 128-byte run)
+  for (int e = 0; e < (1 << eamp); ++e) {
+    const uint32_t t = ((uint32_t)e << lognt) | (uint32_t)tid;
+    sw2::cp_async8(&tile2[sw2::slot(t)], psi + base + off_amp_lo + s_off_amp[e]);
   }
   sw2::cp_async_wait_all();
   __syncthreads();

@@ -304,3 +304,35 @@ def run_job(J, htype: int, seed: int, dt: float, steps: int, prec="c64", a_gener
     st = State(sysm, prec, series_cap=steps + 1)
     st.init_random_phase(seed).evolve(dt, steps)
     return st.polarization(1), st.norm_series(), st
+
+
+def autotune(system: System, prec="c64", candidates=None, probe_steps: int = 4, dt: float = 0.02,
+             seed: int = 1, repeats: int = 2) -> dict:
+    """Pick the tile width K for `system` by timing `probe_steps` Trotter steps
+    of each candidate on the device (CUDA events, best of `repeats`), then set
+    it with spinrp_system_set_tile.  Returns {"K": best, "ms_per_step": {K: ms}}."""
+    import torch
+    p = _PREC[prec]
+    M = system.M
+    if candidates is None:
+        kmax = 14 if p == C64 else 13
+        candidates = [k for k in range(max(2, min(M, kmax) - 4), min(M, kmax) + 1)]
+    timings = {}
+    for K in candidates:
+        system.set_tile(p, K)
+        st = State(system, p, series_cap=1 + (repeats + 1) * probe_steps)
+        st.init_random_phase(seed)
+        st.evolve(dt, probe_steps)  # warm-up
+        best = float("inf")
+        for _ in range(repeats):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st.evolve(dt, probe_steps)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / probe_steps)
+        timings[K] = best
+        st.close()
+    K_best = min(timings, key=timings.get)
+    system.set_tile(p, K_best)
+    return {"K": K_best, "ms_per_step": timings}

@@ -256,7 +256,8 @@ def test_ladder_m30_sampled():
         got = st.read(idx)
         Pg = st.polarization()
         assert np.max(np.abs(Pg - Pw)) <= TOL_P[prec], prec
-        tol = 1e-12 if prec == "c128" else 3e-7 * 2.0 ** -14.5
+        # FP32: ~86 roundings per amplitude in one step, max over 2^14 samples
+        tol = 1e-12 if prec == "c128" else 4e-6 * 2.0 ** -14.5
         assert np.max(np.abs(got - ref)) < tol, prec
         st.evolve(job.dt, 19)
         N = st.norm_series()
