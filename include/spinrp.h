@@ -194,6 +194,37 @@ int spinrp_state_read(spinrp_state *st, const int64_t *idx, int64_t n, double *o
  * layout is the same after every complete spinrp_evolve call. */
 int spinrp_state_layout(const spinrp_state *st, int32_t *layout, void **psi);
 
+/* ---- allocation-free readout (no counterpart in the paper) --------------- */
+
+/* The paper has no counterpart to this call.
+ *
+ * Polarization P = (N_up - N_dn)/(N_up + N_dn) of spin `site` (1-based) and
+ * the norm N_up + N_dn of a device state the caller owns, written to out[0]
+ * and out[1] (a device buffer of 2 doubles the caller owns), asynchronously on
+ * `stream` (a cudaStream_t; NULL = default stream).
+ *
+ * For callers that cannot allocate device memory (code inside a host
+ * application that owns every device allocation, or a loop that must not let
+ * an allocation synchronize the device): this call allocates nothing.  Its
+ * only scratch, 1216 FP64 partial pairs and a counter (about 19.5 KiB), is a
+ * fixed array in device memory that every GPU loading the library holds until
+ * the process exits.
+ *
+ * psi: 2^M amplitudes, complex64 (prec = SPINRP_C64) or complex128, interleaved
+ * re/im.  layout: NULL when bit n-1 of the index is spin n, else M ints giving
+ * the bit position of each spin (as spinrp_state_layout reports for a
+ * library state).  blocks: reduction blocks, 0 = automatic; more than 1216 is
+ * rejected (SPINRP_EINVAL).  Errors: SPINRP_EINVAL for bad arguments or M > 34,
+ * SPINRP_ECUDA if a CUDA call fails.
+ *
+ * The first call on a device (with that device current) looks up the
+ * scratch array's device address; make that first call before any stream
+ * capture.  Every call shares the one array and clears its counter itself;
+ * calls that overlap on the GPU (different streams, no ordering between them)
+ * race on it and must not be issued. */
+int spinrp_polarization_noalloc(const void *psi, int M, int prec, int site, const int32_t *layout,
+                                int blocks, double *out, void *stream);
+
 /* ---- measurement (no counterpart in the paper) ------------------------- */
 
 /* Kernel kinds for spinrp_profile_read. */

@@ -19,7 +19,7 @@ CSRC = HERE / "csrc"
 OUT = HERE / "_build"
 LIB = OUT / "libspinrp.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "planner.cpp"]
+SOURCES = ["api.cu", "planner.cpp", "noalloc.cu"]
 
 
 def nvcc() -> str:

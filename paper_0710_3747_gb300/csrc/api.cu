@@ -33,6 +33,18 @@ static int fail(int code, const char *fmt, ...) {
   return code;
 }
 
+// Error reporting for the other translation units of the library.
+int spinrp::report_error(int code, const char *msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CUDA_TRY(call)                                                                 \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) return fail(SPINRP_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
 static std::atomic<int64_t> g_launches{0};
 
 extern "C" const char *spinrp_last_error(void) { return g_err.c_str(); }

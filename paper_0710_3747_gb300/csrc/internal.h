@@ -97,6 +97,9 @@ struct Plan {
 
 // Build the plan for the canonical bonds with tiles of K spins whose lowest c
 // physical bits are shared by every tile.  Returns false and sets *err on failure.
+// Set the calling thread's spinrp_last_error() message; returns code.
+int report_error(int code, const char *msg);
+
 bool build_plan(int M, const std::vector<std::pair<int, int>> &bonds, int K, int c, Plan *plan,
                 std::string *err);
 

@@ -86,6 +86,8 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             "spinrp_launch_count": ([], ctypes.c_int64),
             "spinrp_state_transfer_bytes": ([vp, i64p, i64p], ctypes.c_int),
             "spinrp_system_plan_check": ([vp, ctypes.c_int, dp, dp], ctypes.c_int),
+            "spinrp_polarization_noalloc": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p,
+                                             ctypes.c_int, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -106,6 +108,19 @@ def _dp(a: np.ndarray):
 
 def version() -> str:
     return lib().spinrp_version().decode()
+
+
+def polarization_noalloc(psi_ptr: int, M: int, prec, site: int, layout, out_ptr: int,
+                         stream: int = 0, blocks: int = 0):
+    """spinrp_polarization_noalloc: (P, norm) of spin `site` of the device state
+    at psi_ptr into the device buffer out_ptr (2 doubles), allocating nothing.
+    For callers that may not allocate device memory; see include/spinrp.h."""
+    lay = None
+    if layout is not None:
+        lay = (ctypes.c_int32 * M)(*[int(v) for v in layout])
+    _check(lib().spinrp_polarization_noalloc(ctypes.c_void_p(psi_ptr), int(M), _PREC[prec], int(site),
+                                             lay, int(blocks), ctypes.c_void_p(out_ptr),
+                                             ctypes.c_void_p(stream)))
 
 
 def launch_count() -> int:
@@ -270,6 +285,12 @@ class State:
         p = ctypes.c_void_p()
         _check(lib().spinrp_state_layout(self._h, lay, ctypes.byref(p)))
         return list(lay)
+
+    def device_ptr(self) -> int:
+        """Device address of the amplitude buffer."""
+        p = ctypes.c_void_p()
+        _check(lib().spinrp_state_layout(self._h, None, ctypes.byref(p)))
+        return int(p.value)
 
     def profile(self, enable: bool = True):
         _check(lib().spinrp_profile(self._h, int(bool(enable))))
