@@ -69,6 +69,24 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def max_over_ranks(x: float, dist=None) -> float:
+    """The largest of x over all ranks (x itself without a process group).
+    Replicas each time their own job; the job-wide time is the slowest rank's."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job throughput of `world` replicas that each process
+    units_per_rank in (the slowest rank's) `seconds`."""
+    return world * units_per_rank / seconds
+
+
 def updates_per_job(M: int, nbonds: int, steps: int) -> float:
     # 2B half-step bond gates per Trotter step, each touching the 2^M-amplitude state
     return float(2 ** M) * 2 * nbonds * steps
@@ -184,6 +202,55 @@ def run_reference(args, rank: int):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def run_batch(args, rank: int, world: int, local_rank: int):
+    """Batched dipolar stars (M uniform in 12..22, dt 0.02): every job of the
+    batch evolved together, sweeps of each plan group as one launch, steady
+    steps replayed as one CUDA graph.  One bench step = init + all steps."""
+    import torch
+
+    from paper_0710_3747_gb300 import spinrp
+    from paper_0710_3747_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    spinrp.lib()
+    jobs = W.star_batch(n=args.batch_jobs, seed=4 + rank, steps=args.batch_steps)
+    systems = [spinrp.System(j.J, j.htype) for j in jobs]
+    b = spinrp.Batch(systems, [j.seed for j in jobs], "c64", series_cap=args.batch_steps + 1)
+    upd = sum(updates_per_job(j.M, j.M * (j.M - 1) // 2, args.batch_steps) for j in jobs)
+
+    def one():
+        b.init_random_phase()
+        b.evolve(0.02, args.batch_steps)
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    n0 = spinrp.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(str(local_rank)) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            one()
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    mean, std = b.ensemble()
+    info = b.info()
+    out = {"metric": METRIC, "value": world * upd / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"star_batch_{args.batch_jobs}jobs_M12-22_dt0.02_{args.batch_steps}steps",
+                      "jobs": args.batch_jobs, "groups": info["groups"], "device_bytes": info["device_bytes"],
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "gpu_launches": spinrp.launch_count() - n0, "clocks": clk.summary(),
+           "ensemble": {"P_mean_end": float(mean[-1]), "P_spread_end": float(std[-1]),
+                        "P_mean_t1": float(mean[len(mean) // 10]),
+                        "P_spread_t1": float(std[len(std) // 10])}}
+    if rank == 0:
+        print(json.dumps(out))
+    return 0
+
+
 def run_ours(args, rank: int, world: int, local_rank: int):
     import torch
 
@@ -237,15 +304,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     launches = spinrp.launch_count() - n0
     st.profile(False)
     ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     P32 = st.polarization()
     sweep_ms, sweep_n = st.profile_read(spinrp.KERNEL_SWEEP)
     init_ms, init_n = st.profile_read(spinrp.KERNEL_INIT)
     upd = updates_per_job(job.M, nb, job.steps)
-    value = world * upd / (ms / 1e3)
+    value = replica_value(upd, ms / 1e3, world)
 
     # roofline of the tile-sweep kernel
     peaks, peak_src = _peaks()
@@ -311,10 +375,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             _, _, h2d, d2h = e2e_job()
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.steps
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, dist)
         out["e2e"] = {"value": world * upd / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h), "s_per_step": e2e_s}
 
@@ -359,7 +420,10 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="ladder_m30", choices=["ladder_m30", "star_m20", "ladder_m14", "ladder_m26"])
+    ap.add_argument("--workload", default="ladder_m30",
+                    choices=["ladder_m30", "star_m20", "ladder_m14", "ladder_m26", "star_batch"])
+    ap.add_argument("--batch-jobs", type=int, default=4096)
+    ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--cpu-gates", type=int, default=43)
     ap.add_argument("--ref-gates", type=int, default=16)
@@ -371,6 +435,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "star_batch" and args.impl == "ours":
+        return run_batch(args, rank, world, local_rank)
     if args.impl == "reference":
         return run_reference(args, rank)
     return run_ours(args, rank, world, local_rank)

@@ -194,6 +194,45 @@ int spinrp_state_read(spinrp_state *st, const int64_t *idx, int64_t n, double *o
  * layout is the same after every complete spinrp_evolve call. */
 int spinrp_state_layout(const spinrp_state *st, int32_t *layout, void **psi);
 
+/* ---- batches of independent jobs ------------------------------------------ */
+
+/* A batch evolves many independent random-phase states at once: disorder
+ * realizations and phase seeds, the average over N_alpha realizations of the
+ * paper's Eq. 4 (each job is one W^{alpha}, its P_11 one term of the mean).
+ * Jobs may differ in M and couplings; jobs with the same sweep plan (same M
+ * and bond structure) form a group whose sweeps run as one launch over all
+ * its jobs, and the steady-state Trotter steps of all groups are replayed as
+ * one CUDA graph.  Device memory (states, tables, series) is allocated by the
+ * library with cudaMalloc. */
+typedef struct spinrp_batch spinrp_batch;
+
+/* Create a batch of njobs jobs: systems[k] (copied; the caller may destroy it
+ * afterwards) with phase seed seeds[k], precision prec, room for series_cap
+ * P(t) entries per job, all work on `stream`.  Errors: SPINRP_EINVAL,
+ * SPINRP_ENOMEM, SPINRP_ECUDA. */
+int spinrp_batch_create(int njobs, const spinrp_system *const *systems, const uint64_t *seeds,
+                        int prec, int64_t series_cap, void *stream, spinrp_batch **out);
+
+/* Free a batch (synchronizes its stream; NULL ignored). */
+void spinrp_batch_destroy(spinrp_batch *b);
+
+/* Device bytes the batch holds, and the number of plan groups. */
+int spinrp_batch_info(const spinrp_batch *b, size_t *device_bytes, int *groups);
+
+/* Random-phase state of every job (seeds from create); records P(0). */
+int spinrp_batch_init_random_phase(spinrp_batch *b);
+
+/* `steps` second-order Trotter steps of size dt for every job (order 2). */
+int spinrp_batch_evolve(spinrp_batch *b, double dt, int64_t steps, int order);
+
+/* P(t) series of job k (site 1) to the host; synchronizes. */
+int spinrp_batch_polarization(spinrp_batch *b, int job, double *out, int64_t cap, int64_t *n);
+
+/* Mean and standard deviation over all jobs of P(t_k), k = 0..len-1 (the
+ * N_alpha average of Eq. 4 and its spread), reduced on the device in FP64;
+ * either output may be NULL.  Synchronizes. */
+int spinrp_batch_ensemble(spinrp_batch *b, double *mean, double *stddev, int64_t cap, int64_t *n);
+
 /* ---- allocation-free readout (no counterpart in the paper) --------------- */
 
 /* The paper has no counterpart to this call.

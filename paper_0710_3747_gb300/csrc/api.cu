@@ -193,10 +193,11 @@ struct PassSet {
   int head = -1, mid = -1, join = -1, tail = -1;
   std::vector<int> body, bodyr;
   int only = -1, first = -1, midstep = -1, last = -1;
+  bool phased = false;  // the register-blocked programs are in use
 };
 
 struct Layout {  // byte offsets inside the work buffer
-  size_t series, partials, ticket, coefs, bvals, adiag, qdiag, passes, ops, phases, rops, stage,
+  size_t series, partials, ticket, job, coefs, bvals, adiag, qdiag, passes, ops, phases, rops, stage,
       stage_idx, total;
 };
 
@@ -235,6 +236,11 @@ struct spinrp_state {
   bool v2 = false;
   double2 *stage = nullptr;
   int64_t *stage_idx = nullptr;
+  JobPtrs *d_job = nullptr;   // this state's pointer table (one job)
+  int64_t *d_step = nullptr;  // device series counter
+  // CUDA graphs of kGraphSteps steady-state Trotter steps (captured on first use)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graphs[2] = {nullptr, nullptr};
   // measurement
   bool prof = false;
   std::vector<cudaEvent_t> ev[3];  // start/stop pairs per kernel kind
@@ -400,7 +406,8 @@ static Layout work_layout(int M, int nb, int64_t cap, const PassSet &ps, int max
   size_t o = 0;
   L.series = o, o = align256(o + sizeof(double) * 2 * std::max<int64_t>(cap, 1));
   L.partials = o, o = align256(o + sizeof(double2) * max_blocks);
-  L.ticket = o, o = align256(o + 256);
+  L.ticket = o, o = align256(o + 256);  // ticket at +0, series counter at +64
+  L.job = o, o = align256(o + sizeof(JobPtrs));
   L.coefs = o, o = align256(o + sizeof(GateCoef) * 2 * std::max(nb, 1));
   L.bvals = o, o = align256(o + sizeof(double) * std::max(nb, 1));
   L.adiag = o, o = align256(o + sizeof(double) * M * M);
@@ -429,6 +436,7 @@ static bool compile_phases(PassSet *ps, int K, std::string *err) {
   for (PassDesc &d : ps->desc) {
     d.phase0 = (int)ps->phases.size();
     d.nphases = 0;
+    d.rop0 = (int)ps->rops.size();
     std::vector<ROp> pending;  // element-wise ops waiting for the next phase
     auto new_phase = [&](const std::vector<int> &rb) {
       PhaseDesc ph;
@@ -449,6 +457,9 @@ static bool compile_phases(PassSet *ps, int K, std::string *err) {
       int nw = 0;
       for (int b : free_bits)
         if (!((used >> b) & 1)) ph.warps[nw++] = (uint8_t)b;
+      for (int k = 0; k < kRegBits; ++k) ph.sm[k] = (uint16_t)swizzle_slot(1u << ph.rb[k]);
+      for (int k = 0; k < 5; ++k) ph.tslot[k] = (uint16_t)swizzle_slot(1u << ph.lanes[k]);
+      for (int k = 0; k < K - 10; ++k) ph.tslot[5 + k] = (uint16_t)swizzle_slot(1u << ph.warps[k]);
       ph.op0 = (int)ps->rops.size();
       ph.nops = 0;
       for (const ROp &r : pending) ps->rops.push_back(r), ph.nops++;
@@ -469,8 +480,17 @@ static bool compile_phases(PassSet *ps, int K, std::string *err) {
       Plan pp;
       if (!build_plan(K, pairs, kRegBits, 0, &pp, err)) return false;
       for (int k = 0; k < pp.segments(); ++k) {
-        new_phase(pp.segQ[k]);
-        const std::vector<int> &rb = pp.segQ[k];
+        // register bit 0 is the pack bit of the complex64 kernel: the bit the
+        // fewest of this phase's gates touch (their arithmetic is scalar)
+        std::vector<int> rb = pp.segQ[k];
+        int pack = 0, best = 1 << 30;
+        for (int q = 0; q < (int)rb.size(); ++q) {
+          int n = 0;
+          for (const PlanGate &g : pp.seg[k]) n += (g.i == rb[q]) + (g.j == rb[q]);
+          if (n < best) best = n, pack = q;
+        }
+        std::rotate(rb.begin(), rb.begin() + pack, rb.begin() + pack + 1);
+        new_phase(rb);
         for (const PlanGate &g : pp.seg[k]) {
           int ku = (int)(std::find(rb.begin(), rb.end(), g.i) - rb.begin());
           int kv = (int)(std::find(rb.begin(), rb.end(), g.j) - rb.begin());
@@ -511,6 +531,11 @@ static bool compile_phases(PassSet *ps, int K, std::string *err) {
     }
     if (!flush(gates)) return false;
     if (!pending.empty() || d.nphases == 0) new_phase({0, 1, 2, 3, 4});
+    d.nrops = (int)ps->rops.size() - d.rop0;
+    if (d.nphases > kMaxPassPhases || d.nrops > kMaxPassOps) {
+      *err = "a sweep's register program exceeds the staging capacity";
+      return false;
+    }
   }
   return true;
 }
@@ -519,9 +544,12 @@ static int plan_state(const spinrp_system &sys, int prec, Plan *plan, PassSet *p
   int rc = make_plan(sys, prec, plan);
   if (rc) return rc;
   build_passes(*plan, any_diag(sys), ps);
+  ps->phased = false;
   if (use_phases(prec, plan->K)) {
+    // a program too large to stage in shared memory runs the plain kernel
     std::string err;
-    if (!compile_phases(ps, plan->K, &err)) return fail(SPINRP_EINVAL, "phases: %s", err.c_str());
+    ps->phased = compile_phases(ps, plan->K, &err);
+    if (!ps->phased) ps->phases.clear(), ps->rops.clear();
   }
   // every gate on two distinct bits of its tile; every store permutation a permutation
   for (const PassDesc &d : ps->desc) {
@@ -558,6 +586,9 @@ extern "C" int spinrp_state_bytes(const spinrp_system *sys, int prec, int64_t se
 static void free_state(spinrp_state *st) {
   if (!st) return;
   prof_clear(st);
+  for (cudaGraphExec_t g : st->graphs)
+    if (g) cudaGraphExecDestroy(g);
+  if (st->cap_stream) cudaStreamDestroy(st->cap_stream);
   if (st->own_psi && st->psi) cudaFree(st->psi);
   if (st->own_work && st->work) cudaFree(st->work);
   delete st;
@@ -641,9 +672,21 @@ extern "C" int spinrp_state_create(const spinrp_system *sys, int prec, void *str
   st->ops = (Op *)(w + st->lay.ops);
   st->phases = (PhaseDesc *)(w + st->lay.phases);
   st->rops = (ROp *)(w + st->lay.rops);
-  st->v2 = use_phases(prec, st->plan.K);
+  st->v2 = st->ps.phased;
   st->stage = (double2 *)(w + st->lay.stage);
   st->stage_idx = (int64_t *)(w + st->lay.stage_idx);
+  st->d_step = (int64_t *)(w + st->lay.ticket + 64);
+  st->d_job = (JobPtrs *)(w + st->lay.job);
+  JobPtrs hj;
+  hj.psi = st->psi;
+  hj.coefs = st->coefs;
+  hj.qdiag = st->qdiag;
+  hj.partials = st->partials;
+  hj.ticket = st->ticket;
+  hj.step = st->d_step;
+  hj.series = st->series;
+  hj.bvals = st->d_bvals;
+  hj.a = st->d_a;
 
   auto up = [&](void *dst, const void *src, size_t n) -> cudaError_t {
     if (n == 0) return cudaSuccess;
@@ -651,6 +694,7 @@ extern "C" int spinrp_state_create(const spinrp_system *sys, int prec, void *str
     return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st->stream);
   };
   if ((e = cudaMemsetAsync(st->ticket, 0, 256, st->stream)) != cudaSuccess ||
+      (e = up(st->d_job, &hj, sizeof hj)) != cudaSuccess ||
       (e = up(st->d_bvals, st->bvals.data(), sizeof(double) * st->bvals.size())) != cudaSuccess ||
       (e = up(st->d_a, st->a.data(), sizeof(double) * st->a.size())) != cudaSuccess ||
       (e = up(st->passes, st->ps.desc.data(), sizeof(PassDesc) * st->ps.desc.size())) != cudaSuccess ||
@@ -689,11 +733,9 @@ extern "C" int spinrp_state_init_random_phase(spinrp_state *st, uint64_t seed) {
   prof_mark(st, SPINRP_KERNEL_INIT);
   ++g_launches;
   if (st->prec == SPINRP_C64)
-    init_kernel<float><<<blocks, 256, 0, st->stream>>>((float2 *)st->psi, st->M, layout_arg(st), seed,
-                                                        st->partials, st->ticket, st->series, 0);
+    init_kernel<float><<<blocks, 256, 0, st->stream>>>(st->d_job, st->M, layout_arg(st), seed, nullptr);
   else
-    init_kernel<double><<<blocks, 256, 0, st->stream>>>((double2 *)st->psi, st->M, layout_arg(st), seed,
-                                                         st->partials, st->ticket, st->series, 0);
+    init_kernel<double><<<blocks, 256, 0, st->stream>>>(st->d_job, st->M, layout_arg(st), seed, nullptr);
   CUDA_TRY(cudaGetLastError());
   prof_mark(st, SPINRP_KERNEL_INIT);
   st->len = 1;
@@ -731,11 +773,9 @@ extern "C" int spinrp_state_load(spinrp_state *st, const double *amps) {
   const int blocks = init_blocks(st->M);
   ++g_launches;
   if (st->prec == SPINRP_C64)
-    observe_kernel<float><<<blocks, 256, 0, st->stream>>>((const float2 *)st->psi, st->M, st->plan.pos[0],
-                                                           st->partials, st->ticket, st->series, 0);
+    observe_kernel<float><<<blocks, 256, 0, st->stream>>>(st->d_job, st->M, st->plan.pos[0]);
   else
-    observe_kernel<double><<<blocks, 256, 0, st->stream>>>((const double2 *)st->psi, st->M, st->plan.pos[0],
-                                                            st->partials, st->ticket, st->series, 0);
+    observe_kernel<double><<<blocks, 256, 0, st->stream>>>(st->d_job, st->M, st->plan.pos[0]);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(st->stream));
   st->len = 1;
@@ -778,58 +818,189 @@ extern "C" int spinrp_state_layout(const spinrp_state *st, int32_t *layout, void
   return SPINRP_OK;
 }
 
+// What the launch helpers need to run a plan over njobs jobs (a state is a
+// plan with one job; a batch has one context per plan group).
+struct LaunchCtx {
+  int M = 0, K = 0;
+  bool v2 = false;
+  int segments = 1, sweeps_per_step = 1;
+  const PassSet *ps = nullptr;
+  const PassDesc *passes = nullptr;
+  const Op *ops = nullptr;
+  const PhaseDesc *phases = nullptr;
+  const ROp *rops = nullptr;
+  const JobPtrs *jobs = nullptr;
+  int njobs = 1;
+  spinrp_state *prof = nullptr;  // state whose profiling marks to record, if any
+};
+
+// Launch one sweep on `stream`; `live` launches are counted and profiled,
+// launches recorded into a graph are not.
 template <typename R>
-static int launch_pass(spinrp_state *st, int pass, int64_t slot) {
-  const int K = st->plan.K;
+static int launch_pass(const LaunchCtx &c, int pass, cudaStream_t stream, bool live) {
+  const int K = c.K;
   const int nt = std::min(512, std::max(32, 1 << K));
   const size_t smem = sizeof(typename CT<R>::T) << K;
-  const unsigned blocks = 1u << (st->M - K);
-  prof_mark(st, SPINRP_KERNEL_SWEEP);
-  ++g_launches;
-  if (sizeof(R) == 4 && st->v2) {
-    sweep2_kernel<<<blocks, 1 << (K - 5), size_t(8) << K, st->stream>>>(
-        (float2 *)st->psi, st->passes + pass, st->phases, st->rops, st->coefs, st->qdiag, st->M,
-        st->partials, st->ticket, st->series, slot);
-    CUDA_TRY(cudaGetLastError());
-    prof_mark(st, SPINRP_KERNEL_SWEEP);
-    return SPINRP_OK;
+  const dim3 grid(1u << (c.M - K), (unsigned)c.njobs);
+  if (live) {
+    if (c.prof) prof_mark(c.prof, SPINRP_KERNEL_SWEEP);
+    ++g_launches;
   }
-  sweep_kernel<R><<<blocks, nt, smem, st->stream>>>(
-      (typename CT<R>::T *)st->psi, st->passes + pass, st->ops, st->coefs, st->qdiag, st->M,
-      st->partials, st->ticket, st->series, slot);
+  if (sizeof(R) == 4 && c.v2)
+    sweep2_kernel<<<grid, 1 << (K - 5), size_t(8) << K, stream>>>(c.jobs, c.passes + pass, c.phases,
+                                                                   c.rops, c.M);
+  else
+    sweep_kernel<R><<<grid, nt, smem, stream>>>(c.jobs, c.passes + pass, c.ops, c.M);
   CUDA_TRY(cudaGetLastError());
-  prof_mark(st, SPINRP_KERNEL_SWEEP);
+  if (live && c.prof) prof_mark(c.prof, SPINRP_KERNEL_SWEEP);
+  return SPINRP_OK;
+}
+
+#define RUN(pass)                                           \
+  do {                                                      \
+    int rc_ = launch_pass<R>(c, (pass), stream, live);      \
+    if (rc_) return rc_;                                    \
+  } while (0)
+
+// n steady-state Trotter steps (neither the first nor the last of a call):
+// [body, middle, reverse body, join] or, for one segment, [whole step].
+template <typename R>
+static int steady_steps(const LaunchCtx &c, cudaStream_t stream, int64_t n, bool live) {
+  const PassSet &ps = *c.ps;
+  for (int64_t k = 0; k < n; ++k) {
+    if (c.segments == 1) {
+      RUN(ps.midstep);
+    } else {
+      for (int id : ps.body) RUN(id);
+      RUN(ps.mid);
+      for (int id : ps.bodyr) RUN(id);
+      RUN(ps.join);
+    }
+  }
+  return SPINRP_OK;
+}
+
+// First step of an evolve call of `steps` steps (the whole call when steps == 1
+// and the plan has one segment).
+template <typename R>
+static int first_step(const LaunchCtx &c, cudaStream_t stream, int64_t steps, bool live) {
+  const PassSet &ps = *c.ps;
+  if (c.segments == 1) RUN(steps == 1 ? ps.only : ps.first);
+  else RUN(ps.head);
   return SPINRP_OK;
 }
 
 template <typename R>
-static int run_evolve(spinrp_state *st, int64_t steps) {
-  const PassSet &ps = st->ps;
-  int64_t slot = st->len;  // slot of the P recorded after the next step
-#define RUN(pass, sl)                                  \
-  do {                                                 \
-    int rc_ = launch_pass<R>(st, (pass), (sl));        \
-    if (rc_) return rc_;                               \
-  } while (0)
-  if (st->plan.segments() == 1) {
-    if (steps == 1) {
-      RUN(ps.only, slot);
-    } else {
-      RUN(ps.first, slot++);
-      for (int64_t n = 1; n + 1 < steps; ++n) RUN(ps.midstep, slot++);
-      RUN(ps.last, slot);
-    }
+static int last_step(const LaunchCtx &c, cudaStream_t stream, int64_t steps, bool live) {
+  const PassSet &ps = *c.ps;
+  if (c.segments == 1) {
+    if (steps > 1) RUN(ps.last);
   } else {
-    RUN(ps.head, -1);
-    for (int64_t n = 0; n < steps; ++n) {
-      for (int id : ps.body) RUN(id, -1);
-      RUN(ps.mid, -1);
-      for (int id : ps.bodyr) RUN(id, -1);
-      RUN(n + 1 < steps ? ps.join : ps.tail, slot++);
-    }
+    for (int id : ps.body) RUN(id);
+    RUN(ps.mid);
+    for (int id : ps.bodyr) RUN(id);
+    RUN(ps.tail);
   }
-#undef RUN
   return SPINRP_OK;
+}
+#undef RUN
+
+static int64_t steady_count(const LaunchCtx &c, int64_t steps) {
+  return c.segments == 1 ? std::max<int64_t>(0, steps - 2) : steps - 1;
+}
+
+constexpr int kGraphSteps = 16;  // steady-state steps per captured CUDA graph
+
+// Capture kGraphSteps steady steps of every context into one graph.
+template <typename R>
+static int capture_graph(const std::vector<LaunchCtx> &cs, cudaStream_t *cap_stream,
+                         cudaGraphExec_t *exec) {
+  if (!*cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(cap_stream, cudaStreamNonBlocking));
+  CUDA_TRY(cudaStreamBeginCapture(*cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = SPINRP_OK;
+  for (int k = 0; k < kGraphSteps && rc == SPINRP_OK; ++k)
+    for (const LaunchCtx &c : cs)
+      if (rc == SPINRP_OK) rc = steady_steps<R>(c, *cap_stream, 1, false);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(*cap_stream, &g);
+  if (rc != SPINRP_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc != SPINRP_OK ? rc : fail(SPINRP_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  }
+  const cudaError_t e2 = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) {
+    *exec = nullptr;
+    return fail(SPINRP_ECUDA, "graph instantiate: %s", cudaGetErrorString(e2));
+  }
+  return SPINRP_OK;
+}
+
+// `steps` Trotter steps of every context (all share dt and steps): the first
+// step, the steady steps (as graph replays when `use_graph`), the last step.
+template <typename R>
+static int run_steps(const std::vector<LaunchCtx> &cs, cudaStream_t stream, int64_t steps,
+                     bool use_graph, cudaStream_t *cap_stream, cudaGraphExec_t *graph) {
+  for (const LaunchCtx &c : cs) {
+    int rc = first_step<R>(c, stream, steps, true);
+    if (rc) return rc;
+  }
+  // every context has the same number of steady steps except single-segment
+  // plans (two fewer instead of one); handle them separately
+  std::vector<LaunchCtx> multi, single;
+  for (const LaunchCtx &c : cs) (c.segments == 1 ? single : multi).push_back(c);
+  for (int pass = 0; pass < 2; ++pass) {
+    const std::vector<LaunchCtx> &group = pass == 0 ? multi : single;
+    if (group.empty()) continue;
+    int64_t left = steady_count(group[0], steps);
+    cudaGraphExec_t *gexec = graph + pass;
+    if (use_graph && left >= kGraphSteps) {
+      if (!*gexec) {
+        int rc = capture_graph<R>(group, cap_stream, gexec);
+        if (rc) return rc;
+      }
+      int64_t per = 0;
+      for (const LaunchCtx &c : group) per += c.segments == 1 ? 1 : c.sweeps_per_step;
+      for (; left >= kGraphSteps; left -= kGraphSteps) {
+        CUDA_TRY(cudaGraphLaunch(*gexec, stream));
+        g_launches += (int64_t)kGraphSteps * per;
+      }
+    }
+    for (int64_t k = 0; k < left; ++k)
+      for (const LaunchCtx &c : group) {
+        int rc = steady_steps<R>(c, stream, 1, true);
+        if (rc) return rc;
+      }
+  }
+  for (const LaunchCtx &c : cs) {
+    int rc = last_step<R>(c, stream, steps, true);
+    if (rc) return rc;
+  }
+  return SPINRP_OK;
+}
+
+static LaunchCtx state_ctx(spinrp_state *st) {
+  LaunchCtx c;
+  c.M = st->M;
+  c.K = st->plan.K;
+  c.v2 = st->v2;
+  c.segments = st->plan.segments();
+  c.sweeps_per_step = st->plan.sweeps_per_step();
+  c.ps = &st->ps;
+  c.passes = st->passes;
+  c.ops = st->ops;
+  c.phases = st->phases;
+  c.rops = st->rops;
+  c.jobs = st->d_job;
+  c.njobs = 1;
+  c.prof = st;
+  return c;
+}
+
+template <typename R>
+static int run_evolve(spinrp_state *st, int64_t steps) {
+  return run_steps<R>({state_ctx(st)}, st->stream, steps, !st->prof, &st->cap_stream, st->graphs);
 }
 
 extern "C" int spinrp_evolve(spinrp_state *st, double dt, int64_t steps, int order) {
@@ -845,13 +1016,13 @@ extern "C" int spinrp_evolve(spinrp_state *st, double dt, int64_t steps, int ord
     prof_mark(st, SPINRP_KERNEL_TABLES);
     if (st->nb > 0) {
       ++g_launches;
-      coef_kernel<<<(2 * st->nb + 127) / 128, 128, 0, st->stream>>>(st->d_bvals, st->nb, dt, st->coefs);
+      coef_kernel<<<(2 * st->nb + 127) / 128, 128, 0, st->stream>>>(st->d_job, st->nb, dt);
       CUDA_TRY(cudaGetLastError());
     }
     if (st->has_diag) {
       const int n = 2 * st->M * st->M;
       ++g_launches;
-      diag_kernel<<<(n + 127) / 128, 128, 0, st->stream>>>(st->d_a, layout_arg(st), st->M, dt, st->qdiag);
+      diag_kernel<<<(n + 127) / 128, 128, 0, st->stream>>>(st->d_job, layout_arg(st), st->M, dt);
       CUDA_TRY(cudaGetLastError());
     }
     prof_mark(st, SPINRP_KERNEL_TABLES);
@@ -991,10 +1162,13 @@ std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint
       uint32_t t0 = 0;
       for (int k = 0; k < 5; ++k) t0 |= ((uint32_t)(tid >> k) & 1u) << ph.lanes[k];
       for (int k = 0; k < K - 10; ++k) t0 |= ((uint32_t)(tid >> (5 + k)) & 1u) << ph.warps[k];
+      uint32_t s0 = 0;  // as the kernel forms it: XOR of the thread-index bits' slots
+      for (int b = 0; b < K - 5; ++b)
+        if ((tid >> b) & 1) s0 ^= ph.tslot[b];
       for (int i = 0; i < 32; ++i) {
-        uint32_t t = t0, s = host_slot(t0);
+        uint32_t t = t0, s = s0;
         for (int k = 0; k < 5; ++k)
-          if ((i >> k) & 1) t |= 1u << ph.rb[k], s ^= host_slot(1u << ph.rb[k]);
+          if ((i >> k) & 1) t |= 1u << ph.rb[k], s ^= ph.sm[k];
         if (t >= T || s != host_slot(t) || s >= T || seen[s]++) {
           snprintf(buf, sizeof buf, "phase %d subcube index out of place (t=%u)", p, t);
           return buf;
@@ -1033,7 +1207,7 @@ extern "C" int spinrp_system_plan_check(const spinrp_system *sys, int prec, doub
   if (phases_per_sweep) *phases_per_sweep = 0.0;
   if (gates_per_phase) *gates_per_phase = 0.0;
   const int K = plan.K;
-  if (!use_phases(prec, K)) return SPINRP_OK;
+  if (!ps.phased) return SPINRP_OK;
   const size_t T = size_t(1) << K;
   std::mt19937_64 rng(12345);
   std::normal_distribution<double> nd;
@@ -1091,5 +1265,331 @@ extern "C" int spinrp_system_plan_check(const spinrp_system *sys, int prec, doub
   }
   if (phases_per_sweep) *phases_per_sweep = ps.desc.empty() ? 0.0 : double(nphase) / ps.desc.size();
   if (gates_per_phase) *gates_per_phase = ngate_phase ? double(ngates) / ngate_phase : 0.0;
+  return SPINRP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+namespace {
+
+// Mean and standard deviation over jobs of P(t_k) (FP64, two passes).
+__global__ void ensemble_kernel(const JobPtrs *__restrict__ jobs, int njobs, int64_t len,
+                                double *__restrict__ out) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < len;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < njobs; ++j) s += jobs[j].series[2 * t];
+    const double mean = s / njobs;
+    double v = 0.0;
+    for (int j = 0; j < njobs; ++j) {
+      const double d = jobs[j].series[2 * t] - mean;
+      v += d * d;
+    }
+    out[t] = mean;
+    out[len + t] = sqrt(v / njobs);
+  }
+}
+
+struct BatchGroup {
+  std::vector<int> jobs;  // batch job indices
+  int M = 0, nb = 0, max_blocks = 0;
+  bool has_diag = false;
+  Plan plan;
+  PassSet ps;
+  LaunchCtx ctx;
+  std::vector<uint8_t> logical_of;
+  unsigned char *dev = nullptr;
+  JobPtrs *d_jobs = nullptr;
+  uint64_t *d_seeds = nullptr;
+};
+
+}  // namespace
+
+struct spinrp_batch {
+  int prec = 0;
+  cudaStream_t stream = nullptr;
+  int64_t cap = 0, len = 0;
+  bool ready = false;
+  double coef_dt = NAN;
+  std::vector<BatchGroup> groups;
+  std::vector<JobPtrs> hjobs;  // every job's device pointers (host copy)
+  JobPtrs *d_all = nullptr;    // the same table on the device (ensemble)
+  double *d_ens = nullptr;     // 2 * cap doubles
+  unsigned char *dev_common = nullptr;
+  size_t bytes = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graphs[2] = {nullptr, nullptr};
+};
+
+static void free_batch(spinrp_batch *b) {
+  if (!b) return;
+  for (cudaGraphExec_t g : b->graphs)
+    if (g) cudaGraphExecDestroy(g);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (auto &g : b->groups)
+    if (g.dev) cudaFree(g.dev);
+  if (b->dev_common) cudaFree(b->dev_common);
+  delete b;
+}
+
+extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *systems,
+                                   const uint64_t *seeds, int prec, int64_t series_cap, void *stream,
+                                   spinrp_batch **out) {
+  if (!out) return fail(SPINRP_EINVAL, "batch_create: out is NULL");
+  *out = nullptr;
+  if (njobs < 1 || njobs > 65535 || !systems || !seeds || series_cap < 1 ||
+      (prec != SPINRP_C64 && prec != SPINRP_C128))
+    return fail(SPINRP_EINVAL, "batch_create: bad argument");
+  spinrp_batch *b = new (std::nothrow) spinrp_batch;
+  if (!b) return fail(SPINRP_ENOMEM, "batch_create: out of host memory");
+  b->prec = prec;
+  b->stream = (cudaStream_t)stream;
+  b->cap = series_cap;
+  b->hjobs.resize(njobs);
+  // group jobs by sweep plan: same M, bond list, diagonal part and tile width
+  for (int k = 0; k < njobs; ++k) {
+    const spinrp_system *s = systems[k];
+    if (!s) {
+      free_batch(b);
+      return fail(SPINRP_EINVAL, "batch_create: system %d is NULL", k);
+    }
+    int gi = -1;
+    for (size_t g = 0; g < b->groups.size() && gi < 0; ++g) {
+      const spinrp_system *r = systems[b->groups[g].jobs[0]];
+      if (r->M == s->M && r->bonds == s->bonds && any_diag(*r) == any_diag(*s) &&
+          r->tileK[prec] == s->tileK[prec])
+        gi = (int)g;
+    }
+    if (gi < 0) {
+      b->groups.emplace_back();
+      gi = (int)b->groups.size() - 1;
+    }
+    b->groups[gi].jobs.push_back(k);
+  }
+  const size_t amp = prec == SPINRP_C64 ? 8 : 16;
+  for (BatchGroup &g : b->groups) {
+    const spinrp_system &s0 = *systems[g.jobs[0]];
+    g.M = s0.M;
+    g.nb = (int)s0.bonds.size();
+    g.has_diag = any_diag(s0);
+    int rc = plan_state(s0, prec, &g.plan, &g.ps, &g.max_blocks);
+    if (rc) {
+      free_batch(b);
+      return rc;
+    }
+    g.logical_of.assign(g.M, 0);
+    for (int q = 0; q < g.M; ++q) g.logical_of[g.plan.pos[q]] = (uint8_t)q;
+    const int n = (int)g.jobs.size(), M = g.M, nb = std::max(g.nb, 1);
+    // one allocation: shared program, job table, seeds, then per-job blocks
+    size_t o = 0;
+    const size_t o_pass = o; o = align256(o + sizeof(PassDesc) * g.ps.desc.size());
+    const size_t o_ops = o; o = align256(o + sizeof(Op) * std::max<size_t>(g.ps.ops.size(), 1));
+    const size_t o_ph = o; o = align256(o + sizeof(PhaseDesc) * std::max<size_t>(g.ps.phases.size(), 1));
+    const size_t o_rop = o; o = align256(o + sizeof(ROp) * std::max<size_t>(g.ps.rops.size(), 1));
+    const size_t o_jobs = o; o = align256(o + sizeof(JobPtrs) * n);
+    const size_t o_seeds = o; o = align256(o + sizeof(uint64_t) * n);
+    const size_t o_job0 = o;
+    size_t per = 0;
+    const size_t p_psi = per; per = align256(per + (amp << M));
+    const size_t p_series = per; per = align256(per + sizeof(double) * 2 * series_cap);
+    const size_t p_part = per; per = align256(per + sizeof(double2) * g.max_blocks);
+    const size_t p_tick = per; per = align256(per + 256);
+    const size_t p_coef = per; per = align256(per + sizeof(GateCoef) * 2 * nb);
+    const size_t p_bv = per; per = align256(per + sizeof(double) * nb);
+    const size_t p_a = per; per = align256(per + sizeof(double) * M * M);
+    const size_t p_q = per; per = align256(per + sizeof(uint64_t) * 2 * M * M);
+    const size_t total = o_job0 + per * n;
+    cudaError_t e = cudaMalloc((void **)&g.dev, total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      free_batch(b);
+      return fail(SPINRP_ENOMEM, "batch_create: cudaMalloc(%zu): %s", total, cudaGetErrorString(e));
+    }
+    b->bytes += total;
+    unsigned char *d = g.dev;
+    g.d_jobs = (JobPtrs *)(d + o_jobs);
+    g.d_seeds = (uint64_t *)(d + o_seeds);
+    std::vector<JobPtrs> hj(n);
+    std::vector<uint64_t> hs(n);
+    std::vector<double> bv(nb), am(M * M);
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+      return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, b->stream) : cudaSuccess;
+    };
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+      const spinrp_system &s = *systems[g.jobs[k]];
+      unsigned char *j = d + o_job0 + per * k;
+      JobPtrs &p = hj[k];
+      p.psi = j + p_psi;
+      p.series = (double *)(j + p_series);
+      p.partials = (double2 *)(j + p_part);
+      p.ticket = (unsigned *)(j + p_tick);
+      p.step = (int64_t *)(j + p_tick + 64);
+      p.coefs = (GateCoef *)(j + p_coef);
+      p.bvals = (double *)(j + p_bv);
+      p.a = (double *)(j + p_a);
+      p.qdiag = (uint64_t *)(j + p_q);
+      hs[k] = seeds[g.jobs[k]];
+      for (int q = 0; q < g.nb; ++q) bv[q] = s.b[s.bonds[q].first * M + s.bonds[q].second];
+      for (int q = 0; q < M * M; ++q) am[q] = s.a[q];
+      if ((e = cudaMemsetAsync(j + p_tick, 0, 256, b->stream)) == cudaSuccess &&
+          (e = up(j + p_bv, bv.data(), sizeof(double) * g.nb)) == cudaSuccess)
+        e = up(j + p_a, am.data(), sizeof(double) * M * M);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // bv/am are reused
+      b->hjobs[g.jobs[k]] = p;
+    }
+    if (e == cudaSuccess && (e = up(d + o_pass, g.ps.desc.data(), sizeof(PassDesc) * g.ps.desc.size())) == cudaSuccess &&
+        (e = up(d + o_ops, g.ps.ops.data(), sizeof(Op) * g.ps.ops.size())) == cudaSuccess &&
+        (e = up(d + o_ph, g.ps.phases.data(), sizeof(PhaseDesc) * g.ps.phases.size())) == cudaSuccess &&
+        (e = up(d + o_rop, g.ps.rops.data(), sizeof(ROp) * g.ps.rops.size())) == cudaSuccess &&
+        (e = up(g.d_jobs, hj.data(), sizeof(JobPtrs) * n)) == cudaSuccess)
+      e = up(g.d_seeds, hs.data(), sizeof(uint64_t) * n);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+      free_batch(b);
+      return fail(SPINRP_ECUDA, "batch_create: upload: %s", cudaGetErrorString(e));
+    }
+    LaunchCtx &c = g.ctx;
+    c.M = M;
+    c.K = g.plan.K;
+    c.v2 = g.ps.phased;
+    c.segments = g.plan.segments();
+    c.sweeps_per_step = g.plan.sweeps_per_step();
+    c.ps = &g.ps;
+    c.passes = (const PassDesc *)(d + o_pass);
+    c.ops = (const Op *)(d + o_ops);
+    c.phases = (const PhaseDesc *)(d + o_ph);
+    c.rops = (const ROp *)(d + o_rop);
+    c.jobs = g.d_jobs;
+    c.njobs = n;
+  }
+  // the LaunchCtx keep pointers to their group's PassSet: fix them now that
+  // the group vector no longer moves
+  for (BatchGroup &g : b->groups) g.ctx.ps = &g.ps;
+  const size_t common = align256(sizeof(JobPtrs) * njobs) + sizeof(double) * 2 * series_cap;
+  cudaError_t e = cudaMalloc((void **)&b->dev_common, common);
+  if (e == cudaSuccess) {
+    b->d_all = (JobPtrs *)b->dev_common;
+    b->d_ens = (double *)(b->dev_common + align256(sizeof(JobPtrs) * njobs));
+    e = cudaMemcpyAsync(b->d_all, b->hjobs.data(), sizeof(JobPtrs) * njobs, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_batch(b);
+    return fail(SPINRP_ENOMEM, "batch_create: %s", cudaGetErrorString(e));
+  }
+  b->bytes += common;
+  int rc = prec == SPINRP_C64 ? set_smem_limits<float>() : set_smem_limits<double>();
+  if (rc) {
+    free_batch(b);
+    return rc;
+  }
+  *out = b;
+  return SPINRP_OK;
+}
+
+extern "C" void spinrp_batch_destroy(spinrp_batch *b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  free_batch(b);
+}
+
+extern "C" int spinrp_batch_info(const spinrp_batch *b, size_t *device_bytes, int *groups) {
+  if (!b) return fail(SPINRP_EINVAL, "batch_info: batch is NULL");
+  if (device_bytes) *device_bytes = b->bytes;
+  if (groups) *groups = (int)b->groups.size();
+  return SPINRP_OK;
+}
+
+static LayoutArg group_layout(const BatchGroup &g) {
+  LayoutArg la;
+  memset(&la, 0, sizeof la);
+  for (int p = 0; p < g.M; ++p) la.logical_of[p] = g.logical_of[p];
+  return la;
+}
+
+extern "C" int spinrp_batch_init_random_phase(spinrp_batch *b) {
+  if (!b) return fail(SPINRP_EINVAL, "batch_init: batch is NULL");
+  for (BatchGroup &g : b->groups) {
+    const dim3 grid(init_blocks(g.M), (unsigned)g.jobs.size());
+    ++g_launches;
+    if (b->prec == SPINRP_C64)
+      init_kernel<float><<<grid, 256, 0, b->stream>>>(g.d_jobs, g.M, group_layout(g), 0, g.d_seeds);
+    else
+      init_kernel<double><<<grid, 256, 0, b->stream>>>(g.d_jobs, g.M, group_layout(g), 0, g.d_seeds);
+    CUDA_TRY(cudaGetLastError());
+  }
+  b->len = 1;
+  b->ready = true;
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_batch_evolve(spinrp_batch *b, double dt, int64_t steps, int order) {
+  if (!b) return fail(SPINRP_EINVAL, "batch_evolve: batch is NULL");
+  if (order != 2) return fail(SPINRP_EUNSUPPORTED, "batch_evolve: only order 2 is implemented");
+  if (!b->ready) return fail(SPINRP_ESTATE, "batch_evolve: batch not initialized");
+  if (!std::isfinite(dt) || steps < 0) return fail(SPINRP_EINVAL, "batch_evolve: bad dt or steps");
+  if (steps == 0) return SPINRP_OK;
+  if (b->len + steps > b->cap)
+    return fail(SPINRP_EINVAL, "batch_evolve: series capacity %lld exceeded", (long long)b->cap);
+  if (!(dt == b->coef_dt)) {
+    for (BatchGroup &g : b->groups) {
+      const unsigned n = (unsigned)g.jobs.size();
+      if (g.nb > 0) {
+        ++g_launches;
+        coef_kernel<<<dim3((2 * g.nb + 127) / 128, n), 128, 0, b->stream>>>(g.d_jobs, g.nb, dt);
+        CUDA_TRY(cudaGetLastError());
+      }
+      if (g.has_diag) {
+        ++g_launches;
+        diag_kernel<<<dim3((2 * g.M * g.M + 127) / 128, n), 128, 0, b->stream>>>(g.d_jobs, group_layout(g),
+                                                                                  g.M, dt);
+        CUDA_TRY(cudaGetLastError());
+      }
+    }
+    b->coef_dt = dt;
+  }
+  std::vector<LaunchCtx> cs;
+  for (BatchGroup &g : b->groups) cs.push_back(g.ctx);
+  const int rc = b->prec == SPINRP_C64
+                     ? run_steps<float>(cs, b->stream, steps, true, &b->cap_stream, b->graphs)
+                     : run_steps<double>(cs, b->stream, steps, true, &b->cap_stream, b->graphs);
+  if (rc) return rc;
+  b->len += steps;
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_batch_polarization(spinrp_batch *b, int job, double *out, int64_t cap, int64_t *n) {
+  if (!b || !n || job < 0 || job >= (int)b->hjobs.size() || (cap > 0 && !out))
+    return fail(SPINRP_EINVAL, "batch_polarization: bad argument");
+  *n = b->len;
+  const int64_t m = std::min(cap, b->len);
+  if (m <= 0) return SPINRP_OK;
+  std::vector<double> buf(2 * m);
+  CUDA_TRY(cudaMemcpyAsync(buf.data(), b->hjobs[job].series, sizeof(double) * 2 * m,
+                           cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  for (int64_t k = 0; k < m; ++k) out[k] = buf[2 * k];
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_batch_ensemble(spinrp_batch *b, double *mean, double *stddev, int64_t cap,
+                                     int64_t *n) {
+  if (!b || !n) return fail(SPINRP_EINVAL, "batch_ensemble: bad argument");
+  *n = b->len;
+  const int64_t len = b->len, m = std::min(cap, len);
+  if (len <= 0 || m <= 0) return SPINRP_OK;
+  ++g_launches;
+  ensemble_kernel<<<(unsigned)((len + 127) / 128), 128, 0, b->stream>>>(b->d_all, (int)b->hjobs.size(),
+                                                                          len, b->d_ens);
+  CUDA_TRY(cudaGetLastError());
+  std::vector<double> buf(2 * len);
+  CUDA_TRY(cudaMemcpyAsync(buf.data(), b->d_ens, sizeof(double) * 2 * len, cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  for (int64_t k = 0; k < m; ++k) {
+    if (mean) mean[k] = buf[k];
+    if (stddev) stddev[k] = buf[len + k];
+  }
   return SPINRP_OK;
 }

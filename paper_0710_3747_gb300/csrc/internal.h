@@ -1,6 +1,7 @@
 // internal.h -- structures shared by the host planner and the device kernels.
 #pragma once
 #include <stdint.h>
+#include <vector_types.h>
 
 #include <string>
 #include <utility>
@@ -41,7 +42,9 @@ struct PassDesc {
   uint8_t outer_pos[kMaxM];
   uint8_t perm[kMaxK];  // store: output tile bit q takes the amplitude bit of input tile bit perm[q]
   int32_t phase0;       // register-blocked program (complex64 path): first phase
-  int32_t nphases;      //   and number of phases
+  int32_t nphases;      //   and number of phases,
+  int32_t rop0;         //   first op
+  int32_t nrops;        //   and number of ops
 };
 
 // Register-blocked execution of a pass (complex64 path).  In a phase every
@@ -57,7 +60,19 @@ struct PhaseDesc {
   uint8_t nops;
   uint8_t pad;
   int32_t op0;
+  uint16_t sm[kRegBits];     // shared-memory slot of each register bit
+  uint16_t tslot[kMaxK - 5]; // slot of each thread-index bit (lanes, then warps)
+  uint16_t pad2;
 };
+
+// A pass's register-blocked program is staged in shared memory; passes with
+// more phases or ops than this run the plain sweep kernel instead.
+constexpr int kMaxPassPhases = 96;
+constexpr int kMaxPassOps = 768;
+
+// Shared-memory slot of tile index t in the register-blocked kernel: the low
+// four bits are XORed with bits 4-7, 8-11 and 12-15 (XOR-linear).
+inline uint32_t swizzle_slot(uint32_t t) { return t ^ (((t >> 4) ^ (t >> 8) ^ (t >> 12)) & 15u); }
 
 // Op of a phase: GATE acts on register bits given by `combo` (pair index
 // 0..9 of (ku < kv) in lexicographic order); DIAG / REDUCE as in Op.
@@ -67,6 +82,22 @@ struct ROp {
   uint8_t arg;
   uint8_t pad;
   int32_t coef;
+};
+
+struct GateCoef;
+
+// Device pointers of one job (one state) as the kernels see them; a launch
+// covers gridDim.y jobs that share one sweep plan, block row y using jobs[y].
+struct JobPtrs {
+  void *psi;               // 2^M amplitudes (float2 or double2)
+  const GateCoef *coefs;   // 2 * bonds gate coefficients (dt/2, dt)
+  const uint64_t *qdiag;   // 2 * M * M fixed-point pair phases (dt/2, dt), physical indexing
+  double2 *partials;       // one (N_up, N_dn) pair per block of a launch
+  unsigned *ticket;        // blocks finished in the current reducing launch
+  int64_t *step;           // entries recorded in `series` so far
+  double *series;          // (P, norm) per recorded step
+  const double *bvals;     // flip-flop coupling of each bond (for the gate tables)
+  const double *a;         // M * M S^zS^z couplings, logical indexing (for the phase tables)
 };
 
 // Gate coefficients of exp(-i theta sigma_x) on a flip-flop pair, theta = b tau/2,

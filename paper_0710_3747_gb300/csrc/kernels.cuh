@@ -84,10 +84,13 @@ __device__ __forceinline__ C cmul(C a, C b) {
   return r;
 }
 
-// Deterministic grid reduction of (N_up, N_dn): block partials in FP64, the
-// last block to finish sums them in block order and writes (P, norm).
-__device__ void reduce_finalize(double up, double dn, double2 *partials, unsigned *ticket,
-                                double *series, int64_t slot) {
+// Deterministic grid reduction of (N_up, N_dn) for the job of this block row:
+// block partials in FP64, the last block to finish sums them in block order,
+// appends (P, norm) to the job's series at its step counter (slot 0 when
+// `reset`) and advances the counter.
+__device__ void reduce_finalize(double up, double dn, const JobPtrs &jp, bool reset) {
+  double2 *partials = jp.partials;
+  unsigned *ticket = jp.ticket;
   __shared__ double s_up[32], s_dn[32];
   __shared__ int s_last;
   for (int o = 16; o; o >>= 1) {
@@ -123,8 +126,10 @@ __device__ void reduce_finalize(double up, double dn, double2 *partials, unsigne
   if (threadIdx.x == 0) {
     double U = 0.0, D = 0.0;
     for (int w = 0; w < nw; ++w) U += s_up[w], D += s_dn[w];
-    series[2 * slot] = (U - D) / (U + D);
-    series[2 * slot + 1] = U + D;
+    const int64_t slot = reset ? 0 : *jp.step;
+    jp.series[2 * slot] = (U - D) / (U + D);
+    jp.series[2 * slot + 1] = U + D;
+    *jp.step = slot + 1;
     *ticket = 0u;
   }
 }
@@ -134,9 +139,12 @@ __device__ void reduce_finalize(double up, double dn, double2 *partials, unsigne
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(256)
-init_kernel(typename CT<R>::T *__restrict__ psi, int M, LayoutArg lay, uint64_t seed,
-            double2 *partials, unsigned *ticket, double *series, int64_t slot) {
+init_kernel(const JobPtrs *__restrict__ jobs, int M, LayoutArg lay, uint64_t seed0,
+            const uint64_t *__restrict__ seeds) {
   using C = typename CT<R>::T;
+  const JobPtrs jp = jobs[blockIdx.y];
+  C *__restrict__ psi = static_cast<C *>(jp.psi);
+  const uint64_t seed = seeds ? seeds[blockIdx.y] : seed0;
   const uint64_t N = 1ull << M;
   const R amp = (R)exp2(-0.5 * (double)(M - 1));
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -167,16 +175,17 @@ init_kernel(typename CT<R>::T *__restrict__ psi, int M, LayoutArg lay, uint64_t 
     }
     psi[y] = v;
   }
-  reduce_finalize((double)up, (double)dn, partials, ticket, series, slot);
+  reduce_finalize((double)up, (double)dn, jp, true);
 }
 
 // ---------------------------------------------------------------------------
 // Per-evolve FP64 tables.
 // ---------------------------------------------------------------------------
-__global__ void coef_kernel(const double *__restrict__ bvals, int nb, double dt,
-                            GateCoef *__restrict__ out) {
+__global__ void coef_kernel(const JobPtrs *__restrict__ jobs, int nb, double dt) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= 2 * nb) return;
+  const double *__restrict__ bvals = jobs[blockIdx.y].bvals;
+  GateCoef *__restrict__ out = const_cast<GateCoef *>(jobs[blockIdx.y].coefs);
   const double tau = (k & 1) ? dt : 0.5 * dt;
   const double th = 0.5 * bvals[k >> 1] * tau;  // exp(-i tau b (SxSx+SySy)) = cos th - i sin th sigma_x
   const double s = sin(th), h = sin(0.5 * th);
@@ -204,10 +213,11 @@ __global__ void coef_kernel(const double *__restrict__ bvals, int nb, double dt,
 // q[v][p][p'] (physical positions): turns of the pair phase -tau_v a_ij / 4 (the
 // phase of e^{-i tau a_ij s_i s_j} for s_i s_j = +1/4), as 64-bit fixed point.
 // tau_0 = dt/2, tau_1 = dt.
-__global__ void diag_kernel(const double *__restrict__ a, LayoutArg lay, int M, double dt,
-                            uint64_t *__restrict__ q) {
+__global__ void diag_kernel(const JobPtrs *__restrict__ jobs, LayoutArg lay, int M, double dt) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= 2 * M * M) return;
+  const double *__restrict__ a = jobs[blockIdx.y].a;
+  uint64_t *__restrict__ q = const_cast<uint64_t *>(jobs[blockIdx.y].qdiag);
   const int v = k / (M * M), p = (k / M) % M, p2 = k % M;
   uint64_t val = 0;
   if (p != p2) {
@@ -252,11 +262,13 @@ __device__ __forceinline__ void rotate<double>(double2 &a, double2 &b, double cm
 
 template <typename R>
 __global__ void __launch_bounds__(512)
-sweep_kernel(typename CT<R>::T *__restrict__ psi, const PassDesc *__restrict__ pdesc,
-             const Op *__restrict__ ops, const GateCoef *__restrict__ coefs,
-             const uint64_t *__restrict__ qdiag, int M, double2 *partials, unsigned *ticket,
-             double *series, int64_t slot) {
+sweep_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pdesc,
+             const Op *__restrict__ ops, int M) {
   using C = typename CT<R>::T;
+  const JobPtrs jp = jobs[blockIdx.y];
+  C *__restrict__ psi = static_cast<C *>(jp.psi);
+  const GateCoef *__restrict__ coefs = jp.coefs;
+  const uint64_t *__restrict__ qdiag = jp.qdiag;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *tile = reinterpret_cast<C *>(smem_raw);
   __shared__ PassDesc d;
@@ -375,7 +387,7 @@ sweep_kernel(typename CT<R>::T *__restrict__ psi, const PassDesc *__restrict__ p
       psi[base + offset(t)] = tile[ti];
     }
   }
-  if (d.has_reduce) reduce_finalize((double)up, (double)dn, partials, ticket, series, slot);
+  if (d.has_reduce) reduce_finalize((double)up, (double)dn, jp, false);
 }
 
 // Gather amplitudes at physical indices into a staging buffer (FP64 pairs).
@@ -404,8 +416,9 @@ __global__ void scatter_kernel(typename CT<R>::T *__restrict__ psi, const int64_
 // Polarization/norm of the whole state (after a load).
 template <typename R>
 __global__ void __launch_bounds__(256)
-observe_kernel(const typename CT<R>::T *__restrict__ psi, int M, int site_pos, double2 *partials,
-               unsigned *ticket, double *series, int64_t slot) {
+observe_kernel(const JobPtrs *__restrict__ jobs, int M, int site_pos) {
+  const JobPtrs jp = jobs[blockIdx.y];
+  const typename CT<R>::T *__restrict__ psi = static_cast<const typename CT<R>::T *>(jp.psi);
   const uint64_t N = 1ull << M;
   double up = 0, dn = 0;
   for (uint64_t y = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; y < N;
@@ -415,7 +428,7 @@ observe_kernel(const typename CT<R>::T *__restrict__ psi, int M, int site_pos, d
     if ((y >> site_pos) & 1ull) up += pr;
     else dn += pr;
   }
-  reduce_finalize(up, dn, partials, ticket, series, slot);
+  reduce_finalize(up, dn, jp, true);
 }
 
 // ===========================================================================
@@ -434,31 +447,94 @@ __device__ __forceinline__ uint32_t slot(uint32_t t) {
   return t ^ (((t >> 4) ^ (t >> 8) ^ (t >> 12)) & 15u);
 }
 
-template <int KU, int KV>
-__device__ __forceinline__ void gate_regs(float2 (&a)[32], float cm1, float s) {
+// Packed FP32x2 arithmetic on 64-bit registers (two lanes per instruction,
+// sm_100 and later).  A pack holds (low lane, high lane) = (bit clear, bit set).
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ u64 pack2(float lo, float hi) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(u64 v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+
+// A thread's 32 amplitudes in a phase are 16 packs: RE[j] = (re with register
+// bit 0 clear, re with it set), IM[j] likewise, j = register bits 1..4.
+// Register bit 0 (the "pack bit") is chosen by the host as the bit with the
+// fewest gates in the phase.
+
+// Gate on register bits (JU + 1, JV + 1): two amplitude pairs per packed
+// instruction.  Same update as rotate<float> (increment formed first).
+template <int JU, int JV>
+__device__ __forceinline__ void gate_packed(u64 (&RE)[16], u64 (&IM)[16], float cm1, float s) {
+  const u64 c2 = pack2(cm1, cm1), s2 = pack2(s, s), n2 = pack2(-s, -s);
 #pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    if (((i >> KU) & 1) == 1 && ((i >> KV) & 1) == 0) {
-      const int j = i ^ (1 << KU) ^ (1 << KV);
-      rotate<float>(a[i], a[j], cm1, s);
+  for (int j = 0; j < 16; ++j) {
+    if (((j >> JU) & 1) == 1 && ((j >> JV) & 1) == 0) {
+      const int k = j ^ (1 << JU) ^ (1 << JV);
+      const u64 ar = RE[j], ai = IM[j], br = RE[k], bi = IM[k];
+      RE[j] = add2(ar, fma2(c2, ar, mul2(s2, bi)));
+      IM[j] = add2(ai, fma2(c2, ai, mul2(n2, br)));
+      RE[k] = add2(br, fma2(c2, br, mul2(s2, ai)));
+      IM[k] = add2(bi, fma2(c2, bi, mul2(n2, ar)));
     }
   }
 }
 
-__device__ __forceinline__ void gate_combo(float2 (&a)[32], int combo, float cm1, float s) {
-  switch (combo) {
-    case 0: gate_regs<0, 1>(a, cm1, s); break;
-    case 1: gate_regs<0, 2>(a, cm1, s); break;
-    case 2: gate_regs<0, 3>(a, cm1, s); break;
-    case 3: gate_regs<0, 4>(a, cm1, s); break;
-    case 4: gate_regs<1, 2>(a, cm1, s); break;
-    case 5: gate_regs<1, 3>(a, cm1, s); break;
-    case 6: gate_regs<1, 4>(a, cm1, s); break;
-    case 7: gate_regs<2, 3>(a, cm1, s); break;
-    case 8: gate_regs<2, 4>(a, cm1, s); break;
-    default: gate_regs<3, 4>(a, cm1, s); break;
+// Gate on the pack bit and register bit JV + 1: the pair is the high lane of
+// pack j (JV clear) and the low lane of pack j + 2^JV; scalar arithmetic.
+template <int JV>
+__device__ __forceinline__ void gate_packbit(u64 (&RE)[16], u64 (&IM)[16], float cm1, float s) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (((j >> JV) & 1) == 0) {
+      const int k = j | (1 << JV);
+      const float2 rj = unpack2(RE[j]), ij = unpack2(IM[j]), rk = unpack2(RE[k]), ik = unpack2(IM[k]);
+      float2 a = make_float2(rj.y, ij.y), b = make_float2(rk.x, ik.x);
+      rotate<float>(a, b, cm1, s);
+      RE[j] = pack2(rj.x, a.x);
+      IM[j] = pack2(ij.x, a.y);
+      RE[k] = pack2(b.x, rk.y);
+      IM[k] = pack2(b.y, ik.y);
+    }
   }
 }
+
+__device__ __forceinline__ void gate_combo(u64 (&RE)[16], u64 (&IM)[16], int combo, float cm1, float s) {
+  switch (combo) {
+    case 0: gate_packbit<0>(RE, IM, cm1, s); break;
+    case 1: gate_packbit<1>(RE, IM, cm1, s); break;
+    case 2: gate_packbit<2>(RE, IM, cm1, s); break;
+    case 3: gate_packbit<3>(RE, IM, cm1, s); break;
+    case 4: gate_packed<0, 1>(RE, IM, cm1, s); break;
+    case 5: gate_packed<0, 2>(RE, IM, cm1, s); break;
+    case 6: gate_packed<0, 3>(RE, IM, cm1, s); break;
+    case 7: gate_packed<1, 2>(RE, IM, cm1, s); break;
+    case 8: gate_packed<1, 3>(RE, IM, cm1, s); break;
+    default: gate_packed<2, 3>(RE, IM, cm1, s); break;
+  }
+}
+
+// lowest set bit of a compile-time g in 1..15 (Gray-code walk)
+__host__ __device__ constexpr int ctz4(int g) { return (g & 1) ? 0 : (g & 2) ? 1 : (g & 4) ? 2 : 3; }
 
 // 8-byte asynchronous global->shared copy (one amplitude): the swizzle may
 // move an amplitude pair to an odd slot, so 16-byte copies would misalign.
@@ -470,21 +546,34 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// A phase op as staged in shared memory: kind, register-bit pair, diagonal
+// variant, and the gate's FP32 coefficients resolved from the job's table.
+struct SOp {
+  uint8_t kind, combo, arg, pad;
+  float cm1, s;
+};
+
 }  // namespace sw2
 
 __global__ void __launch_bounds__(512)
-sweep2_kernel(float2 *__restrict__ psi, const PassDesc *__restrict__ pdesc,
-              const PhaseDesc *__restrict__ phases, const ROp *__restrict__ rops,
-              const GateCoef *__restrict__ coefs, const uint64_t *__restrict__ qdiag, int M,
-              double2 *partials, unsigned *ticket, double *series, int64_t slot) {
+sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pdesc,
+              const PhaseDesc *__restrict__ phases, const ROp *__restrict__ rops, int M) {
+  using sw2::u64;
+  const JobPtrs jp = jobs[blockIdx.y];
+  float2 *__restrict__ psi = static_cast<float2 *>(jp.psi);
+  const GateCoef *__restrict__ coefs = jp.coefs;
+  const uint64_t *__restrict__ qdiag = jp.qdiag;
   extern __shared__ __align__(16) float2 tile2[];
   __shared__ PassDesc d;
   __shared__ uint64_t sH[kMaxK];
   __shared__ uint64_t sQ[kMaxK * kMaxK];
   __shared__ uint64_t sOut;
   __shared__ uint64_t s_off_hi[64];   // physical offset of the high chunk-index bits
-  __shared__ uint32_t s_perm_hi[64];  // input tile index of the high output chunk-index bits
+  __shared__ uint32_t s_slot_st[64];  // slot of the high bits of an output chunk's input index
   __shared__ uint64_t s_off_amp[32];  // physical offset of the high amplitude-index bits
+  __shared__ uint32_t s_slot_amp[32]; // their shared-memory slot (slot is XOR-linear)
+  __shared__ PhaseDesc s_ph[kMaxPassPhases];
+  __shared__ sw2::SOp s_op[kMaxPassOps];
   {
     const int nwords = (int)(sizeof(PassDesc) / 4);
     for (int w = threadIdx.x; w < nwords; w += blockDim.x)
@@ -493,8 +582,20 @@ sweep2_kernel(float2 *__restrict__ psi, const PassDesc *__restrict__ pdesc,
   __syncthreads();
   const int K = d.K, tid = threadIdx.x, nt = blockDim.x;
   const int lognt = 31 - __clz(nt);
-  const uint32_t T = 1u << K;
   const uint64_t base = deposit_bits(blockIdx.x, d.outer_pos, M - K);
+  // stage the pass's program: phases, and ops with their coefficients
+  for (int i = tid; i < d.nphases; i += nt) s_ph[i] = phases[d.phase0 + i];
+  for (int i = tid; i < d.nrops; i += nt) {
+    const ROp r = rops[d.rop0 + i];
+    sw2::SOp o;
+    o.kind = r.kind, o.combo = r.combo, o.arg = r.arg, o.pad = 0;
+    o.cm1 = 0.f, o.s = 0.f;
+    if (r.kind == OP_GATE) {
+      const GateCoef g = coefs[r.coef];
+      o.cm1 = g.cm1f, o.s = g.sf;
+    }
+    s_op[i] = o;
+  }
   // chunks of two amplitudes (tile bit 0): chunk ch = tid + nt * e covers tile
   // index 2*ch; tile bits 1..lognt come from tid, the rest from e
   const int ehi = K - 1 - lognt;  // number of high chunk bits
@@ -506,7 +607,7 @@ sweep2_kernel(float2 *__restrict__ psi, const PassDesc *__restrict__ pdesc,
       if ((e >> k) & 1) o |= 1ull << d.tile_pos[q], pin |= 1u << d.perm[q];
     }
     s_off_hi[e] = o;
-    s_perm_hi[e] = pin;
+    s_slot_st[e] = sw2::slot(pin);
   }
   uint64_t off_lo = 0;
   uint32_t pin_lo = 0;
@@ -514,12 +615,13 @@ sweep2_kernel(float2 *__restrict__ psi, const PassDesc *__restrict__ pdesc,
     if ((tid >> k) & 1) off_lo |= 1ull << d.tile_pos[1 + k], pin_lo |= 1u << d.perm[1 + k];
   // amplitude a = tid + nt * e: tile bits 0..lognt-1 from tid, the K - lognt
   // (= 5) high bits from e
-  const int eamp = K - lognt;
+  constexpr int eamp = 5;
   for (int e = tid; e < (1 << eamp); e += nt) {
     uint64_t o = 0;
     for (int k = 0; k < eamp; ++k)
       if ((e >> k) & 1) o |= 1ull << d.tile_pos[lognt + k];
     s_off_amp[e] = o;
+    s_slot_amp[e] = sw2::slot((uint32_t)e << lognt);
   }
   uint64_t off_amp_lo = 0;
   for (int k = 0; k < lognt; ++k)
@@ -528,30 +630,38 @@ sweep2_kernel(float2 *__restrict__ psi, const PassDesc *__restrict__ pdesc,
 
   // ---- global -> shared (8-byte async copies; 16 consecutive threads read
   // one 128-byte run)
-  for (int e = 0; e < (1 << eamp); ++e) {
-    const uint32_t t = ((uint32_t)e << lognt) | (uint32_t)tid;
-    sw2::cp_async8(&tile2[sw2::slot(t)], psi + base + off_amp_lo + s_off_amp[e]);
+  {
+    const float2 *src = psi + base + off_amp_lo;
+    const uint32_t slot_lo = sw2::slot((uint32_t)tid);
+#pragma unroll
+    for (int e = 0; e < (1 << eamp); ++e)
+      sw2::cp_async8(&tile2[slot_lo ^ s_slot_amp[e]], src + s_off_amp[e]);
   }
   sw2::cp_async_wait_all();
   __syncthreads();
 
   float up = 0.f, dn = 0.f;
   const int nout = M - K;
+  float *tf = reinterpret_cast<float *>(tile2);
   for (int p = 0; p < d.nphases; ++p) {
-    const PhaseDesc ph = phases[d.phase0 + p];
-    // tile index of this thread's subcube origin and register-bit masks
-    uint32_t t0 = 0;
-    for (int k = 0; k < 5; ++k) t0 |= ((uint32_t)(tid >> k) & 1u) << ph.lanes[k];
-    for (int k = 0; k < K - 10; ++k) t0 |= ((uint32_t)(tid >> (5 + k)) & 1u) << ph.warps[k];
-    uint32_t m[5], sm[5];
+    const PhaseDesc &ph = s_ph[p];
+    // slot of this thread's subcube origin (host-precomputed slot of each
+    // thread-index bit) and of the register bits
+    uint32_t s0 = 0;
+    for (int b = 0; b < K - 5; ++b)
+      if ((tid >> b) & 1) s0 ^= ph.tslot[b];
+    uint32_t sm[5];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) m[k] = 1u << ph.rb[k], sm[k] = sw2::slot(m[k]);
-    const uint32_t s0 = sw2::slot(t0);
-    if (ph.nops == 1 && rops[ph.op0].kind == OP_DIAG) {
+    for (int k = 0; k < 5; ++k) sm[k] = ph.sm[k];
+    const int o0 = ph.op0 - d.rop0;
+    if (ph.nops == 1 && s_op[o0].kind == OP_DIAG) {
       // diagonal phase e^{-i tau D}, amplitude by amplitude in shared memory:
       // Theta(x) = sum_{p<p'} q_pp' sigma_p sigma_p' (mod 2^64) split into
       // outer-outer (sOut), outer-tile (sH) and tile-tile (sQ) parts
-      const uint64_t *q = qdiag + (size_t)rops[ph.op0].arg * M * M;
+      uint32_t t0 = 0;
+      for (int k = 0; k < 5; ++k) t0 |= ((uint32_t)(tid >> k) & 1u) << ph.lanes[k];
+      for (int k = 0; k < K - 10; ++k) t0 |= ((uint32_t)(tid >> (5 + k)) & 1u) << ph.warps[k];
+      const uint64_t *q = qdiag + (size_t)s_op[o0].arg * M * M;
       if (tid < K) {
         const int pp = d.tile_pos[tid];
         uint64_t h = 0;
@@ -574,7 +684,7 @@ sweep2_kernel(float2 *__restrict__ psi, const PassDesc *__restrict__ pdesc,
       for (int w = tid; w < K * K; w += nt) sQ[w] = q[d.tile_pos[w / K] * M + d.tile_pos[w % K]];
       __syncthreads();
       uint32_t isreg = 0;
-      for (int k = 0; k < 5; ++k) isreg |= m[k];
+      for (int k = 0; k < 5; ++k) isreg |= 1u << ph.rb[k];
       // fixed part (tile bits from the thread index) once per thread
       uint64_t th0 = sOut;
       for (int x = 0; x < K; ++x) {
@@ -617,56 +727,86 @@ sweep2_kernel(float2 *__restrict__ psi, const PassDesc *__restrict__ pdesc,
       __syncthreads();
       continue;
     }
-    float2 a[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
+    // load the subcube as 16 packs, walking the packs in Gray-code order so
+    // each step changes one register bit (one XOR on the slot)
+    u64 RE[16], IM[16];
+    {
       uint32_t s = s0;
 #pragma unroll
-      for (int k = 0; k < 5; ++k)
-        if ((i >> k) & 1) s ^= sm[k];
-      a[i] = tile2[s];
+      for (int g = 0; g < 16; ++g) {
+        if (g) s ^= sm[1 + sw2::ctz4(g)];
+        const int j = g ^ (g >> 1);
+        const uint32_t s1 = s ^ sm[0];
+        RE[j] = sw2::pack2(tf[2 * s], tf[2 * s1]);
+        IM[j] = sw2::pack2(tf[2 * s + 1], tf[2 * s1 + 1]);
+      }
     }
+    sw2::SOp cur = s_op[o0];
     for (int k = 0; k < ph.nops; ++k) {
-      const ROp op = rops[ph.op0 + k];
-      if (op.kind == OP_GATE) {
-        const GateCoef g = coefs[op.coef];
-        sw2::gate_combo(a, op.combo, g.cm1f, g.sf);
-      } else if (op.kind == OP_REDUCE) {
+      const sw2::SOp nxt = s_op[o0 + (k + 1 < ph.nops ? k + 1 : k)];  // prefetch
+      if (cur.kind == OP_GATE) {
+        sw2::gate_combo(RE, IM, cur.combo, cur.cm1, cur.s);
+      } else if (cur.kind == OP_REDUCE) {
         int kr = -1;
 #pragma unroll
         for (int q = 0; q < 5; ++q)
           if (ph.rb[q] == d.site_tile) kr = q;
-        const uint32_t fixed_bit = d.site_tile >= 0 ? ((t0 >> d.site_tile) & 1u)
-                                                    : (uint32_t)((base >> d.site_pos) & 1ull);
+        uint32_t fixed_bit;
+        if (d.site_tile < 0) {
+          fixed_bit = (uint32_t)((base >> d.site_pos) & 1ull);
+        } else {
+          uint32_t t0 = 0;
+          for (int b = 0; b < 5; ++b) t0 |= ((uint32_t)(tid >> b) & 1u) << ph.lanes[b];
+          for (int b = 0; b < K - 10; ++b) t0 |= ((uint32_t)(tid >> (5 + b)) & 1u) << ph.warps[b];
+          fixed_bit = (t0 >> d.site_tile) & 1u;
+        }
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float pr = a[i].x * a[i].x + a[i].y * a[i].y;
-          const uint32_t bit = kr >= 0 ? ((uint32_t)(i >> kr) & 1u) : fixed_bit;
-          if (bit) up += pr;
-          else dn += pr;
+        for (int j = 0; j < 16; ++j) {
+          const float2 pr = sw2::unpack2(sw2::fma2(RE[j], RE[j], sw2::mul2(IM[j], IM[j])));
+          if (kr == 0) {
+            dn += pr.x;
+            up += pr.y;
+          } else {
+            const uint32_t bit = kr > 0 ? ((uint32_t)(j >> (kr - 1)) & 1u) : fixed_bit;
+            if (bit) up += pr.x + pr.y;
+            else dn += pr.x + pr.y;
+          }
         }
       }
+      cur = nxt;
     }
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
+    {
       uint32_t s = s0;
 #pragma unroll
-      for (int k = 0; k < 5; ++k)
-        if ((i >> k) & 1) s ^= sm[k];
-      tile2[s] = a[i];
+      for (int g = 0; g < 16; ++g) {
+        if (g) s ^= sm[1 + sw2::ctz4(g)];
+        const int j = g ^ (g >> 1);
+        const uint32_t s1 = s ^ sm[0];
+        const float2 r = sw2::unpack2(RE[j]), i = sw2::unpack2(IM[j]);
+        tf[2 * s] = r.x;
+        tf[2 * s + 1] = i.x;
+        tf[2 * s1] = r.y;
+        tf[2 * s1 + 1] = i.y;
+      }
     }
     __syncthreads();
   }
 
   // ---- shared -> global, output tile bits relabelled by perm
-  for (int e = 0; e < (1 << ehi); ++e) {
-    const uint32_t tin = pin_lo | s_perm_hi[e];  // input index of output chunk (tile bit 0 = 0)
-    const float2 v0 = tile2[sw2::slot(tin)];
-    const float2 v1 = tile2[sw2::slot(tin | (1u << d.perm[0]))];
-    float4 *dst = reinterpret_cast<float4 *>(psi + base + off_lo + s_off_hi[e]);
-    *dst = make_float4(v0.x, v0.y, v1.x, v1.y);
+  {
+    // input index of output chunk e = pin_lo | (its high bits), so its slot is
+    // slot(pin_lo) ^ s_slot_st[e]; the chunk's second amplitude is output tile
+    // bit 0 = input tile bit perm[0]
+    const uint32_t sl0 = sw2::slot(pin_lo), sl1 = sw2::slot(1u << d.perm[0]);
+    float2 *dst0 = psi + base + off_lo;
+#pragma unroll 4
+    for (int e = 0; e < (1 << ehi); ++e) {
+      const uint32_t s = sl0 ^ s_slot_st[e];
+      const float2 v0 = tile2[s], v1 = tile2[s ^ sl1];
+      *reinterpret_cast<float4 *>(dst0 + s_off_hi[e]) = make_float4(v0.x, v0.y, v1.x, v1.y);
+    }
   }
-  if (d.has_reduce) reduce_finalize((double)up, (double)dn, partials, ticket, series, slot);
+  if (d.has_reduce) reduce_finalize((double)up, (double)dn, jp, false);
 }
 
 }  // namespace spinrp

@@ -84,14 +84,20 @@ def _finish(a: _Active, now_fn) -> Result:
 
 def run_stream(jobs: list[W.Job], prec: str = "c64", max_active: int = 16,
                hbm_budget: int | None = None, chunk: int = 20, tile_K: int | None = None,
-               realtime: bool = True) -> list[Result]:
+               realtime: bool = True, start_fn=None, finish_fn=None, footprint_fn=None,
+               trace: list | None = None) -> list[Result]:
     """Serve `jobs` (sorted by arrival) with continuous batching.
 
     realtime: arrivals follow the wall clock (t = 0 at the call); otherwise all
     jobs are treated as arrived at their arrival offset but admitted as soon
-    as resources allow (a saturated queue)."""
-    import torch
+    as resources allow (a saturated queue).  start_fn / finish_fn /
+    footprint_fn replace the device calls (host-side tests); `trace`, when
+    given, receives ("admit" | "chunk" | "done", job index, bytes in use)."""
+    footprint_fn = footprint_fn or footprint
+    start_fn = start_fn or _start
+    finish_fn = finish_fn or _finish
     if hbm_budget is None:
+        import torch
         free, _ = torch.cuda.mem_get_info()
         hbm_budget = int(0.8 * free)
     pending = sorted(jobs, key=lambda j: j.arrival)
@@ -107,14 +113,16 @@ def run_stream(jobs: list[W.Job], prec: str = "c64", max_active: int = 16,
             j = pending[k]
             if realtime and j.arrival > now():
                 break
-            need = footprint(j, prec)
+            need = footprint_fn(j, prec)
             if need > hbm_budget:
                 raise spinrp.SpinrpError(spinrp.ENOMEM, f"job {k} needs {need} B > budget {hbm_budget} B")
             if used + need > hbm_budget:
                 break
-            a = _start(j, prec, now(), tile_K)
+            a = start_fn(j, prec, now(), tile_K)
             active.append(a)
             used += a.bytes
+            if trace is not None:
+                trace.append(("admit", a.res.index, used))
             k += 1
         if not active:
             # idle until the next arrival
@@ -126,11 +134,15 @@ def run_stream(jobs: list[W.Job], prec: str = "c64", max_active: int = 16,
             n = min(chunk, a.left)
             a.state.evolve(a.job.dt, n)
             a.left -= n
+            if trace is not None:
+                trace.append(("chunk", a.res.index, used))
         still = []
         for a in active:
             if a.left == 0:
-                done.append(_finish(a, now))
+                done.append(finish_fn(a, now))
                 used -= a.bytes
+                if trace is not None:
+                    trace.append(("done", a.res.index, used))
             else:
                 still.append(a)
         active = still
@@ -138,9 +150,10 @@ def run_stream(jobs: list[W.Job], prec: str = "c64", max_active: int = 16,
 
 
 def run_sequential(jobs: list[W.Job], prec: str = "c64", tile_K: int | None = None,
-                   realtime: bool = True) -> list[Result]:
+                   realtime: bool = True, chunk: int | None = None) -> list[Result]:
     """The same jobs one at a time, each started when it has arrived and the
-    previous one is done."""
+    previous one is done (in evolve calls of `chunk` steps when given, else
+    one call per job)."""
     import torch
     out = []
     t0 = time.perf_counter()
@@ -149,7 +162,11 @@ def run_sequential(jobs: list[W.Job], prec: str = "c64", tile_K: int | None = No
         if realtime and j.arrival > now():
             time.sleep(j.arrival - now())
         a = _start(j, prec, now(), tile_K)
-        a.state.evolve(j.dt, j.steps)
+        left = j.steps
+        while left > 0:
+            n = left if not chunk else min(chunk, left)
+            a.state.evolve(j.dt, n)
+            left -= n
         out.append(_finish(a, now))
     torch.cuda.synchronize()
     return sorted(out, key=lambda r: r.index)

@@ -357,3 +357,92 @@ def autotune(system: System, prec="c64", candidates=None, probe_steps: int = 4, 
     K_best = min(timings, key=timings.get)
     system.set_tile(p, K_best)
     return {"K": K_best, "ms_per_step": timings}
+
+
+# ---------------------------------------------------------------------------
+# batches
+# ---------------------------------------------------------------------------
+_BATCH_SIG = {
+    "spinrp_batch_create": ([ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_uint64),
+                             ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
+                            ctypes.c_int),
+    "spinrp_batch_destroy": ([ctypes.c_void_p], None),
+    "spinrp_batch_info": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int)],
+                          ctypes.c_int),
+    "spinrp_batch_init_random_phase": ([ctypes.c_void_p], ctypes.c_int),
+    "spinrp_batch_evolve": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
+    "spinrp_batch_polarization": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "spinrp_batch_ensemble": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                               ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+}
+
+
+def _batch_lib():
+    L = lib()
+    if not getattr(L, "_batch_sig", False):
+        for name, (args, res) in _BATCH_SIG.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        L._batch_sig = True
+    return L
+
+
+class Batch:
+    """Many independent jobs (systems + phase seeds) evolved together; the
+    N_alpha realizations of the paper's Eq. 4.  Device memory is allocated by
+    the library."""
+
+    def __init__(self, systems: list, seeds, prec="c64", series_cap: int = 1024, stream=None):
+        L = _batch_lib()
+        n = len(systems)
+        self.systems = list(systems)  # keep the handles alive while creating
+        hs = (ctypes.c_void_p * n)(*[s.handle.value for s in systems])
+        sd = (ctypes.c_uint64 * n)(*[int(x) & (2**64 - 1) for x in seeds])
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        h = ctypes.c_void_p()
+        _check(L.spinrp_batch_create(n, hs, sd, _PREC[prec], int(series_cap), ctypes.c_void_p(int(stream)),
+                                     ctypes.byref(h)))
+        self._h = h
+        self.n = n
+
+    def info(self) -> dict:
+        bts, g = ctypes.c_size_t(), ctypes.c_int()
+        _check(_batch_lib().spinrp_batch_info(self._h, ctypes.byref(bts), ctypes.byref(g)))
+        return {"device_bytes": bts.value, "groups": g.value}
+
+    def init_random_phase(self):
+        _check(_batch_lib().spinrp_batch_init_random_phase(self._h))
+        return self
+
+    def evolve(self, dt: float, steps: int, order: int = 2):
+        _check(_batch_lib().spinrp_batch_evolve(self._h, float(dt), int(steps), int(order)))
+        return self
+
+    def polarization(self, job: int) -> np.ndarray:
+        n = ctypes.c_int64()
+        _check(_batch_lib().spinrp_batch_polarization(self._h, int(job), None, 0, ctypes.byref(n)))
+        out = np.empty(max(n.value, 1), dtype=np.float64)
+        _check(_batch_lib().spinrp_batch_polarization(self._h, int(job), _dp(out), n.value, ctypes.byref(n)))
+        return out[:n.value]
+
+    def ensemble(self) -> tuple[np.ndarray, np.ndarray]:
+        """(mean, standard deviation) over jobs of P(t_k), reduced on the device."""
+        n = ctypes.c_int64()
+        _check(_batch_lib().spinrp_batch_ensemble(self._h, None, None, 0, ctypes.byref(n)))
+        mean = np.empty(max(n.value, 1))
+        std = np.empty(max(n.value, 1))
+        _check(_batch_lib().spinrp_batch_ensemble(self._h, _dp(mean), _dp(std), n.value, ctypes.byref(n)))
+        return mean[:n.value], std[:n.value]
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.spinrp_batch_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        self.close()

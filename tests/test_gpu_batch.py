@@ -1,0 +1,65 @@
+"""Batches: many disorder realizations and phase seeds of uneven M evolved
+together (the N_alpha average of the paper's Eq. 4).
+
+Each job of a batch runs the same kernels on the same plan as a single state
+of that system, so its P(t) equals the single-state result bit for bit; a few
+jobs are checked against the FP64 oracle; the device ensemble mean / spread
+equal the host reduction of the per-job series.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0710_3747_gb300 import spinrp
+from paper_0710_3747_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _jobs(n=18, seed=3):
+    jobs = W.star_batch(n=n, seed=seed, m_lo=8, m_hi=14, dt=0.02, steps=40)
+    jobs += [W.Job(W.ladder(5, 1.0, 0.5), W.XY, seed=99, dt=0.02, steps=40, kind="ladder")]
+    return jobs
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_batch_equals_single_states(prec):
+    spinrp.lib()
+    jobs = _jobs()
+    systems = [spinrp.System(j.J, j.htype) for j in jobs]
+    b = spinrp.Batch(systems, [j.seed for j in jobs], prec, series_cap=64)
+    assert b.info()["groups"] >= 4
+    b.init_random_phase()
+    b.evolve(0.02, 25)
+    b.evolve(0.02, 15)
+    for k, j in enumerate(jobs):
+        st = spinrp.State(spinrp.System(j.J, j.htype), prec, series_cap=64)
+        st.init_random_phase(j.seed).evolve(0.02, 25).evolve(0.02, 15)
+        assert np.array_equal(b.polarization(k), st.polarization()), k
+        st.close()
+    tol = 1e-10 if prec == "c128" else 1e-4
+    for k in (0, 5, len(jobs) - 1):
+        j = jobs[k]
+        Pw, _, _ = oracle.run(j.J, j.htype, j.seed, 0.02, 40)
+        assert np.max(np.abs(b.polarization(k) - Pw)) <= tol
+    mean, std = b.ensemble()
+    allP = np.array([b.polarization(k) for k in range(len(jobs))])
+    np.testing.assert_allclose(mean, allP.mean(axis=0), atol=1e-13)
+    np.testing.assert_allclose(std, allP.std(axis=0), atol=1e-13)
+    b.close()
+
+
+def test_batch_spread_shrinks_with_m():
+    """Self-averaging across realizations: the spread of P over seeds of one
+    system falls with M (paper: Chebyshev bound, max p_i = 2^{-(M-1)})."""
+    spinrp.lib()
+    spread = {}
+    for M in (10, 14):
+        J = W.star_dipolar(M, 1)
+        systems = [spinrp.System(J, W.DIPOLAR) for _ in range(32)]
+        b = spinrp.Batch(systems, list(range(1, 33)), "c64", series_cap=32)
+        b.init_random_phase().evolve(0.05, 30)
+        mean, std = b.ensemble()
+        spread[M] = std[10:].mean()
+        b.close()
+    assert spread[14] < spread[10] / 2.5
