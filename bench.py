@@ -215,6 +215,11 @@ def run_batch(args, rank: int, world: int, local_rank: int):
     spinrp.lib()
     jobs = W.star_batch(n=args.batch_jobs, seed=4 + rank, steps=args.batch_steps)
     systems = [spinrp.System(j.J, j.htype) for j in jobs]
+    for s_ in systems:
+        if args.regbits:
+            s_.set_regbits(args.regbits)
+        if args.tile_K:
+            s_.set_tile("c64", min(args.tile_K, s_.M))
     b = spinrp.Batch(systems, [j.seed for j in jobs], "c64", series_cap=args.batch_steps + 1)
     upd = sum(updates_per_job(j.M, j.M * (j.M - 1) // 2, args.batch_steps) for j in jobs)
 
@@ -266,6 +271,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     sysm = spinrp.System(job.J, job.htype)
     if args.tile_K:
         sysm.set_tile(prec, args.tile_K)
+    if args.regbits:
+        sysm.set_regbits(args.regbits)
     nb = len(sysm.bonds())
     info = sysm.plan_info(prec)
     st = spinrp.State(sysm, prec, series_cap=job.steps + 1)
@@ -361,6 +368,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             s2 = spinrp.System(job.J, job.htype)
             if args.tile_K:
                 s2.set_tile(prec, args.tile_K)
+            if args.regbits:
+                s2.set_regbits(args.regbits)
             st2 = spinrp.State(s2, prec, series_cap=job.steps + 1)
             st2.init_random_phase(job.seed + rank).evolve(job.dt, job.steps)
             P = st2.polarization()
@@ -428,6 +437,7 @@ def main():
     ap.add_argument("--cpu-gates", type=int, default=43)
     ap.add_argument("--ref-gates", type=int, default=16)
     ap.add_argument("--tile-K", type=int, default=0, help="tile width override (autotuner knob)")
+    ap.add_argument("--regbits", type=int, default=0, help="register bits per phase, 5 or 6 (autotuner knob)")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")

@@ -115,6 +115,14 @@ int spinrp_system_bonds(const spinrp_system *sys, int32_t *pairs, int cap, int *
  * Errors: SPINRP_EINVAL. */
 int spinrp_system_set_tile(spinrp_system *sys, int prec, int K);
 
+/* Register bits per phase of the complex64 tile kernel: each thread keeps the
+ * 2^rb amplitudes spanned by rb tile bits in registers while it applies every
+ * ready gate on those bits (rb = 5 or 6; 0 restores the default, 5).  Wider
+ * register sets apply more gates per shared-memory round trip with fewer
+ * threads per tile.  The second autotuner knob; affects states and batches
+ * created afterwards.  Errors: SPINRP_EINVAL. */
+int spinrp_system_set_regbits(spinrp_system *sys, int rb);
+
 /* Describe the sweep plan the library would use for precision prec: number
  * of segments the forward half step is cut into (*segments), device sweeps
  * per Trotter step in the steady state (*sweeps_per_step) and the tile width
@@ -160,6 +168,17 @@ void spinrp_state_destroy(spinrp_state *st);
  * times 2^-53, r = the basis index of spins 2..M (spin n at bit n-2).  Resets
  * the series and records P(0).  Asynchronous. */
 int spinrp_state_init_random_phase(spinrp_state *st, uint64_t seed);
+
+/* Set the state to the paper's product (unentangled) random state of the
+ * "Testing the quantum parallelism" section,
+ *   |Psi> = |up>_1 (x) prod_{l=2..M} (|down>_l + e^{-i phi_l} |up>_l)/sqrt 2,
+ * i.e. psi_x = 2^{-(M-1)/2} exp(-i sum_{l up in x} phi_l) for spin 1 up, 0
+ * otherwise: only M-1 independent phases.  phi_l = 2 pi u_l, u_l = top 53 bits
+ * of the first two output words of Philox4x32-10(counter = (l-1, 0, 0, 1),
+ * key = (lo32 seed, hi32 seed)) times 2^-53 (the counter's last word keeps
+ * these draws apart from the entangled state's).  Resets the series and
+ * records P(0).  Asynchronous. */
+int spinrp_state_init_product_phase(spinrp_state *st, uint64_t seed);
 
 /* Load an arbitrary state from the host: 2^M complex amplitudes in logical
  * order as interleaved FP64 (re, im).  Resets the series and records P(0).
@@ -221,6 +240,9 @@ int spinrp_batch_info(const spinrp_batch *b, size_t *device_bytes, int *groups);
 
 /* Random-phase state of every job (seeds from create); records P(0). */
 int spinrp_batch_init_random_phase(spinrp_batch *b);
+
+/* Product random state (as spinrp_state_init_product_phase) of every job. */
+int spinrp_batch_init_product_phase(spinrp_batch *b);
 
 /* `steps` second-order Trotter steps of size dt for every job (order 2). */
 int spinrp_batch_evolve(spinrp_batch *b, double dt, int64_t steps, int order);

@@ -224,3 +224,36 @@ def run(J: np.ndarray, htype: int, seed: int, dt: float, steps: int, a_generic=N
     n0 = float(np.vdot(psi, psi).real)
     P, nrm = evolve(psi, a, b, dt, steps, bonds=bonds, site=site, threads=threads)
     return np.concatenate([[p0], P]), np.concatenate([[n0], nrm]), psi
+
+
+def product_uniform(seed: int, bit: int) -> float:
+    """u_l of the product state's phase of the spin at bit index `bit` (>= 1)."""
+    L = lib()
+    L.oracle_product_uniform.argtypes = [ctypes.c_uint64, ctypes.c_int]
+    L.oracle_product_uniform.restype = ctypes.c_double
+    return float(L.oracle_product_uniform(int(seed) & (2**64 - 1), int(bit)))
+
+
+def init_product_phase(M: int, seed: int, threads: int | None = None) -> np.ndarray:
+    """The paper's product (unentangled) random state: spin 1 up, each other
+    spin l in (|down> + e^{-i phi_l}|up>)/sqrt(2)."""
+    L = lib()
+    L.oracle_init_product_phase.argtypes = [ctypes.c_int, ctypes.c_uint64,
+                                            ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    L.oracle_init_product_phase.restype = ctypes.c_int
+    buf = np.empty(2 * (1 << M), dtype=np.float64)
+    if L.oracle_init_product_phase(M, int(seed) & (2**64 - 1), _dptr(buf), _threads(threads)) != 0:
+        raise ValueError("oracle_init_product_phase failed")
+    return buf.view(np.complex128)
+
+
+def run_product(J: np.ndarray, htype: int, seed: int, dt: float, steps: int, a_generic=None,
+                site: int = 1, threads: int | None = None):
+    """Whole job from the product state: (P[0..steps], norm[0..steps], psi)."""
+    a, b = couplings(J, htype, a_generic)
+    M = a.shape[0]
+    psi = init_product_phase(M, seed, threads)
+    p0 = polarization(psi, site)
+    n0 = float(np.vdot(psi, psi).real)
+    P, nrm = evolve(psi, a, b, dt, steps, site=site, threads=threads)
+    return np.concatenate([[p0], P]), np.concatenate([[n0], nrm]), psi

@@ -108,9 +108,10 @@ def sector_ensemble_polarization(a: np.ndarray, b: np.ndarray, times, site: int 
         sz = np.where((basis >> (site - 1)) & 1, 1.0, -1.0)
         Z = V.T @ (sz[:, None] * V)
         W2 = Z * Z
-        dE = E[:, None] - E[None, :]
-        for ti, t in enumerate(times):
-            acc[ti] += np.sum(W2 * np.cos(dE * t))
+        # sum_mn W2_mn cos((E_m - E_n) t) = Re sum_m e^{-i E_m t} (W2 u)_m, u_n = e^{i E_n t}
+        for t0 in range(0, times.size, 128):
+            u = np.exp(1j * E[:, None] * times[None, t0:t0 + 128])
+            acc[t0:t0 + 128] += np.real(np.sum(np.conj(u) * (W2 @ u), axis=0))
     return acc / (1 << M)
 
 

@@ -268,3 +268,46 @@ int oracle_evolve(int M, double *psi, const double *a, const double *b, const in
     free(ph);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Product (unentangled) random state of the "Testing the quantum            */
+/* parallelism" section: spin 1 up, every other spin l in                     */
+/* (|down> + e^{-i phi_l} |up>)/sqrt(2) with its own random phase:            */
+/*   psi_x = 2^{-(M-1)/2} exp(-i sum_{l up in x, l >= 2} phi_l)  (spin 1 up)  */
+/* phi_l = 2 pi u_l, u_l = top 53 bits of the first two Philox4x32-10 output  */
+/* words for counter (l - 1, 0, 0, 1) (l = 2..M, i.e. bit index l - 1) and   */
+/* key (lo seed, hi seed), times 2^-53.                                       */
+/* ------------------------------------------------------------------------ */
+double oracle_product_uniform(uint64_t seed, int bit)
+{
+    uint32_t ctr[4] = {(uint32_t)bit, 0u, 0u, 1u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    uint64_t bits = ((uint64_t)out[0] << 32) | (uint64_t)out[1];
+    return (double)(bits >> 11) * (1.0 / 9007199254740992.0);
+}
+
+int oracle_init_product_phase(int M, uint64_t seed, double *psi, int nthreads)
+{
+    if (M < 1 || M > 40) return 1;
+    set_threads(nthreads);
+    double phi[64];
+    for (int q = 1; q < M; ++q) phi[q] = ORACLE_TWO_PI * oracle_product_uniform(seed, q);
+    const int64_t N = (int64_t)1 << M;
+    const double amp = pow(2.0, -0.5 * (double)(M - 1));
+#pragma omp parallel for schedule(static)
+    for (int64_t x = 0; x < N; ++x) {
+        if ((x & 1) == 0) {
+            psi[2 * x] = 0.0;
+            psi[2 * x + 1] = 0.0;
+        } else {
+            double th = 0.0;
+            for (int q = 1; q < M; ++q)
+                if ((x >> q) & 1) th -= phi[q];
+            psi[2 * x] = amp * cos(th);
+            psi[2 * x + 1] = amp * sin(th);
+        }
+    }
+    return 0;
+}

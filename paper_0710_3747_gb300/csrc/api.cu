@@ -59,6 +59,7 @@ struct spinrp_system {
   std::vector<double> a, b;  // M*M, symmetric, zero diagonal
   std::vector<std::pair<int, int>> bonds;
   int tileK[2] = {0, 0};
+  int regbits = 0;  // register bits per phase of the complex64 kernel (0: default)
 };
 
 static bool any_diag(const spinrp_system &s) {
@@ -124,7 +125,14 @@ extern "C" int spinrp_system_bonds(const spinrp_system *sys, int32_t *pairs, int
   return SPINRP_OK;
 }
 
-static int default_K(int prec) { return prec == SPINRP_C64 ? 14 : 13; }
+// Default tile width.  complex64: 2^14 amplitudes (128 KiB, one tile per SM)
+// while the state fits in L2 and the sweep is bound by the in-tile work; 2^13
+// (64 KiB, two tiles per SM, one loading while the other computes) for states
+// streamed from HBM.  complex128: 2^13 (128 KiB).
+static int default_K(int prec, int M) {
+  if (prec != SPINRP_C64) return 13;
+  return M >= 25 ? 13 : 14;
+}
 static int low_bits(int prec) { return prec == SPINRP_C64 ? 4 : 3; }  // 128-byte runs
 
 extern "C" int spinrp_system_set_tile(spinrp_system *sys, int prec, int K) {
@@ -136,8 +144,15 @@ extern "C" int spinrp_system_set_tile(spinrp_system *sys, int prec, int K) {
   return SPINRP_OK;
 }
 
+extern "C" int spinrp_system_set_regbits(spinrp_system *sys, int rb) {
+  if (!sys || !(rb == 0 || rb == 5 || rb == 6))
+    return fail(SPINRP_EINVAL, "system_set_regbits: rb must be 0, 5 or 6");
+  sys->regbits = rb;
+  return SPINRP_OK;
+}
+
 static int make_plan(const spinrp_system &s, int prec, Plan *plan) {
-  int K = s.tileK[prec] ? s.tileK[prec] : default_K(prec);
+  int K = s.tileK[prec] ? s.tileK[prec] : default_K(prec, s.M);
   K = std::min(K, s.M);
   std::string err;
   if (!build_plan(s.M, s.bonds, K, low_bits(prec), plan, &err))
@@ -194,6 +209,7 @@ struct PassSet {
   std::vector<int> body, bodyr;
   int only = -1, first = -1, midstep = -1, last = -1;
   bool phased = false;  // the register-blocked programs are in use
+  int rb = 5;           // their register bits per phase
 };
 
 struct Layout {  // byte offsets inside the work buffer
@@ -422,27 +438,33 @@ static Layout work_layout(int M, int nb, int64_t cap, const PassSet &ps, int max
   return L;
 }
 
-// Register-blocked tiles are used for complex64 with K >= 10 (2^(K-5) threads).
-static bool use_phases(int prec, int K) { return prec == SPINRP_C64 && K >= 10; }
+// Register-blocked tiles are used for complex64 when the tile has at least
+// 5 lane bits besides the rb register bits (2^(K-rb) threads).
+static bool use_phases(int prec, int K, int rb) { return prec == SPINRP_C64 && K >= 5 + rb; }
+// Six register bits (fewer phases, so fewer shared-memory round trips per
+// gate) wherever the tile leaves five lane bits; five below that.
+static int default_regbits(int K) { return K >= 11 ? 6 : 5; }
 
-// Compile every pass into phases of five register bits: the pass's gates
+// Compile every pass into phases of RB register bits: the pass's gates
 // between two element-wise ops (diagonal phase, reduction) are cut into
 // phases by the same greedy as the sweep planner (gates on disjoint bits may
 // be exchanged, nothing else), and each element-wise op runs in the phase
 // after the gates it follows.
-static bool compile_phases(PassSet *ps, int K, std::string *err) {
+static bool compile_phases(PassSet *ps, int K, int RB, std::string *err) {
   ps->phases.clear();
   ps->rops.clear();
   for (PassDesc &d : ps->desc) {
     d.phase0 = (int)ps->phases.size();
     d.nphases = 0;
     d.rop0 = (int)ps->rops.size();
+    std::vector<int> default_rb(RB);
+    for (int k = 0; k < RB; ++k) default_rb[k] = k;
     std::vector<ROp> pending;  // element-wise ops waiting for the next phase
     auto new_phase = [&](const std::vector<int> &rb) {
       PhaseDesc ph;
       memset(&ph, 0, sizeof ph);
       uint32_t isreg = 0;
-      for (int k = 0; k < kRegBits; ++k) ph.rb[k] = (uint8_t)rb[k], isreg |= 1u << rb[k];
+      for (int k = 0; k < RB; ++k) ph.rb[k] = (uint8_t)rb[k], isreg |= 1u << rb[k];
       // lane bits: four non-register bits of distinct residues mod 4 (bank-
       // conflict free with the shared-memory swizzle), then the lowest left
       std::vector<int> free_bits, lanes;
@@ -457,9 +479,9 @@ static bool compile_phases(PassSet *ps, int K, std::string *err) {
       int nw = 0;
       for (int b : free_bits)
         if (!((used >> b) & 1)) ph.warps[nw++] = (uint8_t)b;
-      for (int k = 0; k < kRegBits; ++k) ph.sm[k] = (uint16_t)swizzle_slot(1u << ph.rb[k]);
+      for (int k = 0; k < RB; ++k) ph.sm[k] = (uint16_t)swizzle_slot(1u << ph.rb[k]);
       for (int k = 0; k < 5; ++k) ph.tslot[k] = (uint16_t)swizzle_slot(1u << ph.lanes[k]);
-      for (int k = 0; k < K - 10; ++k) ph.tslot[5 + k] = (uint16_t)swizzle_slot(1u << ph.warps[k]);
+      for (int k = 0; k < K - RB - 5; ++k) ph.tslot[5 + k] = (uint16_t)swizzle_slot(1u << ph.warps[k]);
       ph.op0 = (int)ps->rops.size();
       ph.nops = 0;
       for (const ROp &r : pending) ps->rops.push_back(r), ph.nops++;
@@ -478,7 +500,7 @@ static bool compile_phases(PassSet *ps, int K, std::string *err) {
       std::vector<std::pair<int, int>> pairs;
       for (const Op *g : gates) pairs.push_back({g->u, g->v});
       Plan pp;
-      if (!build_plan(K, pairs, kRegBits, 0, &pp, err)) return false;
+      if (!build_plan(K, pairs, RB, 0, &pp, err)) return false;
       for (int k = 0; k < pp.segments(); ++k) {
         // register bit 0 is the pack bit of the complex64 kernel: the bit the
         // fewest of this phase's gates touch (their arithmetic is scalar)
@@ -495,10 +517,12 @@ static bool compile_phases(PassSet *ps, int K, std::string *err) {
           int ku = (int)(std::find(rb.begin(), rb.end(), g.i) - rb.begin());
           int kv = (int)(std::find(rb.begin(), rb.end(), g.j) - rb.begin());
           if (ku > kv) std::swap(ku, kv);
-          static const int base_idx[4] = {0, 4, 7, 9};  // combo = index of (ku,kv) in lexicographic order
+          // combo = index of (ku, kv) among the RB(RB-1)/2 pairs, lexicographic
+          int base_idx = 0;
+          for (int i = 0; i < ku; ++i) base_idx += RB - 1 - i;
           ROp r{};
           r.kind = OP_GATE;
-          r.combo = (uint8_t)(base_idx[ku] + (kv - ku - 1));
+          r.combo = (uint8_t)(base_idx + (kv - ku - 1));
           r.coef = gates[g.bond]->coef;
           push_rop(r);
         }
@@ -519,9 +543,9 @@ static bool compile_phases(PassSet *ps, int K, std::string *err) {
       r.arg = op.arg;
       if (op.kind == OP_DIAG) {
         // the diagonal phase runs alone (its own phase, no register subcube)
-        if (!pending.empty()) new_phase({0, 1, 2, 3, 4});
+        if (!pending.empty()) new_phase(default_rb);
         pending.push_back(r);
-        new_phase({0, 1, 2, 3, 4});
+        new_phase(default_rb);
         last_is_diag = true;
       } else if (d.nphases > 0 && pending.empty() && !last_is_diag) {
         push_rop(r);
@@ -530,7 +554,7 @@ static bool compile_phases(PassSet *ps, int K, std::string *err) {
       }
     }
     if (!flush(gates)) return false;
-    if (!pending.empty() || d.nphases == 0) new_phase({0, 1, 2, 3, 4});
+    if (!pending.empty() || d.nphases == 0) new_phase(default_rb);
     d.nrops = (int)ps->rops.size() - d.rop0;
     if (d.nphases > kMaxPassPhases || d.nrops > kMaxPassOps) {
       *err = "a sweep's register program exceeds the staging capacity";
@@ -545,10 +569,11 @@ static int plan_state(const spinrp_system &sys, int prec, Plan *plan, PassSet *p
   if (rc) return rc;
   build_passes(*plan, any_diag(sys), ps);
   ps->phased = false;
-  if (use_phases(prec, plan->K)) {
+  ps->rb = sys.regbits ? sys.regbits : default_regbits(plan->K);
+  if (use_phases(prec, plan->K, ps->rb)) {
     // a program too large to stage in shared memory runs the plain kernel
     std::string err;
-    ps->phased = compile_phases(ps, plan->K, &err);
+    ps->phased = compile_phases(ps, plan->K, ps->rb, &err);
     if (!ps->phased) ps->phases.clear(), ps->rops.clear();
   }
   // every gate on two distinct bits of its tile; every store permutation a permutation
@@ -601,7 +626,10 @@ static int set_smem_limits() {
   CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(typename CT<R>::T) << kmax)));
   if (sizeof(R) == 4)
-    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
+  {
+    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
+    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
+  }
   return SPINRP_OK;
 }
 
@@ -727,20 +755,30 @@ static LayoutArg layout_arg(const spinrp_state *st) {
   return la;
 }
 
-extern "C" int spinrp_state_init_random_phase(spinrp_state *st, uint64_t seed) {
+static int state_init(spinrp_state *st, uint64_t seed, int kind) {
   if (!st) return fail(SPINRP_EINVAL, "init: state is NULL");
   const int blocks = init_blocks(st->M);
   prof_mark(st, SPINRP_KERNEL_INIT);
   ++g_launches;
   if (st->prec == SPINRP_C64)
-    init_kernel<float><<<blocks, 256, 0, st->stream>>>(st->d_job, st->M, layout_arg(st), seed, nullptr);
+    init_kernel<float><<<blocks, 256, 0, st->stream>>>(st->d_job, st->M, layout_arg(st), seed, nullptr,
+                                                       kind);
   else
-    init_kernel<double><<<blocks, 256, 0, st->stream>>>(st->d_job, st->M, layout_arg(st), seed, nullptr);
+    init_kernel<double><<<blocks, 256, 0, st->stream>>>(st->d_job, st->M, layout_arg(st), seed, nullptr,
+                                                        kind);
   CUDA_TRY(cudaGetLastError());
   prof_mark(st, SPINRP_KERNEL_INIT);
   st->len = 1;
   st->ready = true;
   return SPINRP_OK;
+}
+
+extern "C" int spinrp_state_init_random_phase(spinrp_state *st, uint64_t seed) {
+  return state_init(st, seed, INIT_ENTANGLED);
+}
+
+extern "C" int spinrp_state_init_product_phase(spinrp_state *st, uint64_t seed) {
+  return state_init(st, seed, INIT_PRODUCT);
 }
 
 // physical index of logical basis index x
@@ -831,6 +869,7 @@ struct LaunchCtx {
   const ROp *rops = nullptr;
   const JobPtrs *jobs = nullptr;
   int njobs = 1;
+  int rb = 5;                    // register bits of the register-blocked kernel
   spinrp_state *prof = nullptr;  // state whose profiling marks to record, if any
 };
 
@@ -847,8 +886,14 @@ static int launch_pass(const LaunchCtx &c, int pass, cudaStream_t stream, bool l
     ++g_launches;
   }
   if (sizeof(R) == 4 && c.v2)
-    sweep2_kernel<<<grid, 1 << (K - 5), size_t(8) << K, stream>>>(c.jobs, c.passes + pass, c.phases,
-                                                                   c.rops, c.M);
+  {
+    if (c.rb == 6)
+      sweep2_kernel<6><<<grid, 1 << (K - 6), size_t(8) << K, stream>>>(c.jobs, c.passes + pass, c.phases,
+                                                                        c.rops, c.M);
+    else
+      sweep2_kernel<5><<<grid, 1 << (K - 5), size_t(8) << K, stream>>>(c.jobs, c.passes + pass, c.phases,
+                                                                        c.rops, c.M);
+  }
   else
     sweep_kernel<R><<<grid, nt, smem, stream>>>(c.jobs, c.passes + pass, c.ops, c.M);
   CUDA_TRY(cudaGetLastError());
@@ -985,6 +1030,7 @@ static LaunchCtx state_ctx(spinrp_state *st) {
   c.M = st->M;
   c.K = st->plan.K;
   c.v2 = st->v2;
+  c.rb = st->ps.rb;
   c.segments = st->plan.segments();
   c.sweeps_per_step = st->plan.sweeps_per_step();
   c.ps = &st->ps;
@@ -1128,8 +1174,8 @@ double check_reduce(const std::vector<cplx> &A) {
 // shared-memory slots in range and each touched exactly once per stage.
 uint32_t host_slot(uint32_t t) { return t ^ (((t >> 4) ^ (t >> 8) ^ (t >> 12)) & 15u); }
 
-std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint64_t block) {
-  const int K = d.K, nt = 1 << (K - 5), lognt = K - 5;
+std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint64_t block, int rb) {
+  const int K = d.K, nt = 1 << (K - rb), lognt = K - rb;
   const uint32_t T = 1u << K;
   uint64_t base = 0;
   for (int k = 0; k < M - K; ++k) base |= ((block >> k) & 1ull) << d.outer_pos[k];
@@ -1161,13 +1207,13 @@ std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint
     for (int tid = 0; tid < nt; ++tid) {
       uint32_t t0 = 0;
       for (int k = 0; k < 5; ++k) t0 |= ((uint32_t)(tid >> k) & 1u) << ph.lanes[k];
-      for (int k = 0; k < K - 10; ++k) t0 |= ((uint32_t)(tid >> (5 + k)) & 1u) << ph.warps[k];
+      for (int k = 0; k < lognt - 5; ++k) t0 |= ((uint32_t)(tid >> (5 + k)) & 1u) << ph.warps[k];
       uint32_t s0 = 0;  // as the kernel forms it: XOR of the thread-index bits' slots
-      for (int b = 0; b < K - 5; ++b)
+      for (int b = 0; b < lognt; ++b)
         if ((tid >> b) & 1) s0 ^= ph.tslot[b];
-      for (int i = 0; i < 32; ++i) {
+      for (int i = 0; i < (1 << rb); ++i) {
         uint32_t t = t0, s = s0;
-        for (int k = 0; k < 5; ++k)
+        for (int k = 0; k < rb; ++k)
           if ((i >> k) & 1) t |= 1u << ph.rb[k], s ^= ph.sm[k];
         if (t >= T || s != host_slot(t) || s >= T || seen[s]++) {
           snprintf(buf, sizeof buf, "phase %d subcube index out of place (t=%u)", p, t);
@@ -1216,7 +1262,7 @@ extern "C" int spinrp_system_plan_check(const spinrp_system *sys, int prec, doub
     const PassDesc &d = ps.desc[pi];
     const uint64_t nblocks = 1ull << (plan.M - K);
     for (uint64_t blk : {uint64_t(0), nblocks / 3, nblocks - 1}) {
-      const std::string e = audit_sweep2(d, ps.phases.data(), plan.M, blk);
+      const std::string e = audit_sweep2(d, ps.phases.data(), plan.M, blk, ps.rb);
       if (!e.empty()) return fail(SPINRP_EINVAL, "plan_check: pass %zu block %llu: %s", pi,
                                   (unsigned long long)blk, e.c_str());
     }
@@ -1230,13 +1276,15 @@ extern "C" int spinrp_system_plan_check(const spinrp_system *sys, int prec, doub
       else if (op.kind == OP_DIAG) check_diag(A, op.arg);
       else ra.push_back(check_reduce(A));
     }
-    static const int KU[10] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 3}, KV[10] = {1, 2, 3, 4, 2, 3, 4, 3, 4, 4};
+    std::vector<int> KU, KV;  // combo -> register-bit pair
+    for (int a = 0; a < ps.rb; ++a)
+      for (int bb = a + 1; bb < ps.rb; ++bb) KU.push_back(a), KV.push_back(bb);
     for (int p = 0; p < d.nphases; ++p) {
       const PhaseDesc &ph = ps.phases[d.phase0 + p];
       uint32_t seen = 0;
-      for (int k = 0; k < kRegBits; ++k) seen |= 1u << ph.rb[k];
+      for (int k = 0; k < ps.rb; ++k) seen |= 1u << ph.rb[k];
       for (int k = 0; k < 5; ++k) seen |= 1u << ph.lanes[k];
-      for (int k = 0; k < K - 10; ++k) seen |= 1u << ph.warps[k];
+      for (int k = 0; k < K - ps.rb - 5; ++k) seen |= 1u << ph.warps[k];
       if (seen != (1u << K) - 1u || __builtin_popcount(seen) != K)
         return fail(SPINRP_EINVAL, "plan_check: pass %zu phase %d does not partition the tile bits", pi, p);
       int g = 0;
@@ -1453,6 +1501,7 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
     c.M = M;
     c.K = g.plan.K;
     c.v2 = g.ps.phased;
+    c.rb = g.ps.rb;
     c.segments = g.plan.segments();
     c.sweeps_per_step = g.plan.sweeps_per_step();
     c.ps = &g.ps;
@@ -1509,21 +1558,25 @@ static LayoutArg group_layout(const BatchGroup &g) {
   return la;
 }
 
-extern "C" int spinrp_batch_init_random_phase(spinrp_batch *b) {
+static int batch_init(spinrp_batch *b, int kind) {
   if (!b) return fail(SPINRP_EINVAL, "batch_init: batch is NULL");
   for (BatchGroup &g : b->groups) {
     const dim3 grid(init_blocks(g.M), (unsigned)g.jobs.size());
     ++g_launches;
     if (b->prec == SPINRP_C64)
-      init_kernel<float><<<grid, 256, 0, b->stream>>>(g.d_jobs, g.M, group_layout(g), 0, g.d_seeds);
+      init_kernel<float><<<grid, 256, 0, b->stream>>>(g.d_jobs, g.M, group_layout(g), 0, g.d_seeds, kind);
     else
-      init_kernel<double><<<grid, 256, 0, b->stream>>>(g.d_jobs, g.M, group_layout(g), 0, g.d_seeds);
+      init_kernel<double><<<grid, 256, 0, b->stream>>>(g.d_jobs, g.M, group_layout(g), 0, g.d_seeds, kind);
     CUDA_TRY(cudaGetLastError());
   }
   b->len = 1;
   b->ready = true;
   return SPINRP_OK;
 }
+
+extern "C" int spinrp_batch_init_random_phase(spinrp_batch *b) { return batch_init(b, INIT_ENTANGLED); }
+
+extern "C" int spinrp_batch_init_product_phase(spinrp_batch *b) { return batch_init(b, INIT_PRODUCT); }
 
 extern "C" int spinrp_batch_evolve(spinrp_batch *b, double dt, int64_t steps, int order) {
   if (!b) return fail(SPINRP_EINVAL, "batch_evolve: batch is NULL");

@@ -48,19 +48,19 @@ struct PassDesc {
 };
 
 // Register-blocked execution of a pass (complex64 path).  In a phase every
-// thread holds the 2^5 amplitudes of the tile that differ only in the five
-// tile bits rb[] (its "subcube"), applies the phase's ops to them in registers
-// and writes them back to shared memory.  lanes[]/warps[] give the tile bits
-// the thread index supplies.
-constexpr int kRegBits = 5;
+// thread holds the 2^RB amplitudes of the tile that differ only in the RB
+// tile bits rb[] (its "subcube"; RB = 5 or 6 per plan), applies the phase's
+// ops to them in registers and writes them back to shared memory.
+// lanes[]/warps[] give the tile bits the thread index supplies.
+constexpr int kMaxRegBits = 6;  // 5 or 6 register bits per phase
 struct PhaseDesc {
-  uint8_t rb[kRegBits];
+  uint8_t rb[kMaxRegBits];
   uint8_t lanes[5];
   uint8_t warps[kMaxK - 10];
   uint8_t nops;
   uint8_t pad;
   int32_t op0;
-  uint16_t sm[kRegBits];     // shared-memory slot of each register bit
+  uint16_t sm[kMaxRegBits];  // shared-memory slot of each register bit
   uint16_t tslot[kMaxK - 5]; // slot of each thread-index bit (lanes, then warps)
   uint16_t pad2;
 };
@@ -74,8 +74,9 @@ constexpr int kMaxPassOps = 768;
 // four bits are XORed with bits 4-7, 8-11 and 12-15 (XOR-linear).
 inline uint32_t swizzle_slot(uint32_t t) { return t ^ (((t >> 4) ^ (t >> 8) ^ (t >> 12)) & 15u); }
 
-// Op of a phase: GATE acts on register bits given by `combo` (pair index
-// 0..9 of (ku < kv) in lexicographic order); DIAG / REDUCE as in Op.
+// Op of a phase: GATE acts on register bits given by `combo` (index of the
+// pair (ku < kv) among the RB(RB-1)/2 pairs, lexicographic); DIAG / REDUCE as
+// in Op.
 struct ROp {
   uint8_t kind;
   uint8_t combo;
@@ -126,11 +127,11 @@ struct Plan {
   int sweeps_per_step() const { return seg.size() <= 1 ? 1 : 2 * (int)seg.size() - 2; }
 };
 
-// Build the plan for the canonical bonds with tiles of K spins whose lowest c
-// physical bits are shared by every tile.  Returns false and sets *err on failure.
 // Set the calling thread's spinrp_last_error() message; returns code.
 int report_error(int code, const char *msg);
 
+// Build the plan for the canonical bonds with tiles of K spins whose lowest c
+// physical bits are shared by every tile.  Returns false and sets *err on failure.
 bool build_plan(int M, const std::vector<std::pair<int, int>> &bonds, int K, int c, Plan *plan,
                 std::string *err);
 

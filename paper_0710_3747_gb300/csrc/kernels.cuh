@@ -1,7 +1,8 @@
 // kernels.cuh -- device code of the random-phase Trotter path (sm_103a).
 //
-//   init_kernel   : the paper's entangled random-phase state, phases from an
-//                   in-kernel Philox4x32-10, fused P(0)/norm reduction.
+//   init_kernel   : the paper's entangled random-phase state (or its product
+//                   state), phases from an in-kernel Philox4x32-10, fused
+//                   P(0)/norm reduction.
 //   coef_kernel   : FP64 generation of every flip-flop gate's (cos-1, sin) pair
 //                   for dt/2 and dt, rounded to FP32 with a unitarity-defect search.
 //   diag_kernel   : FP64 -> 64-bit fixed-point turn tables of e^{-i tau a_ij/4 s s}.
@@ -137,10 +138,18 @@ __device__ void reduce_finalize(double up, double dn, const JobPtrs &jp, bool re
 // ---------------------------------------------------------------------------
 // Random-phase initial state.
 // ---------------------------------------------------------------------------
+// kind INIT_ENTANGLED: an independent phase per basis state of spins 2..M.
+// kind INIT_PRODUCT: the paper's product state, spin 1 up and every other spin
+// l in (|down> + e^{-i phi_l}|up>)/sqrt 2, phi_l = 2 pi u_l with u_l the top 53
+// bits of Philox4x32-10(counter = (l-1, 0, 0, 1), key) times 2^-53; the
+// amplitude's phase -sum phi_l over the up spins is summed exactly as 64-bit
+// fixed-point turns.
+enum InitKind { INIT_ENTANGLED = 0, INIT_PRODUCT = 1 };
+
 template <typename R>
 __global__ void __launch_bounds__(256)
 init_kernel(const JobPtrs *__restrict__ jobs, int M, LayoutArg lay, uint64_t seed0,
-            const uint64_t *__restrict__ seeds) {
+            const uint64_t *__restrict__ seeds, int kind) {
   using C = typename CT<R>::T;
   const JobPtrs jp = jobs[blockIdx.y];
   C *__restrict__ psi = static_cast<C *>(jp.psi);
@@ -148,6 +157,20 @@ init_kernel(const JobPtrs *__restrict__ jobs, int M, LayoutArg lay, uint64_t see
   const uint64_t N = 1ull << M;
   const R amp = (R)exp2(-0.5 * (double)(M - 1));
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  // product state: turns u_l * 2^64 of each physical bit position (0 for spin 1)
+  __shared__ uint64_t s_turns[kMaxM];
+  if (kind == INIT_PRODUCT) {
+    for (int p = threadIdx.x; p < M; p += blockDim.x) {
+      const int q = lay.logical_of[p];
+      uint64_t t = 0;
+      if (q > 0) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)q, 0u, 0u, 1u), key);
+        t = ((((uint64_t)w.x << 32) | w.y) >> 11) << 11;
+      }
+      s_turns[p] = t;
+    }
+    __syncthreads();
+  }
   R up = 0, dn = 0;
   for (uint64_t y = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; y < N;
        y += (uint64_t)gridDim.x * blockDim.x) {
@@ -156,6 +179,13 @@ init_kernel(const JobPtrs *__restrict__ jobs, int M, LayoutArg lay, uint64_t see
     C v;
     if ((x & 1ull) == 0) {
       v.x = 0, v.y = 0;
+    } else if (kind == INIT_PRODUCT) {
+      uint64_t th = 0;
+      for (int p = 0; p < M; ++p)
+        if ((y >> p) & 1ull) th -= s_turns[p];
+      const C e = cis_turns(th, (R)0);
+      v.x = amp * e.x, v.y = amp * e.y;
+      up += v.x * v.x + v.y * v.y;
     } else {
       const uint64_t r = x >> 1;
       const uint4 w = philox4x32_10(make_uint4((uint32_t)r, (uint32_t)(r >> 32), 0u, 0u), key);
@@ -476,18 +506,18 @@ __device__ __forceinline__ float2 unpack2(u64 v) {
   return r;
 }
 
-// A thread's 32 amplitudes in a phase are 16 packs: RE[j] = (re with register
-// bit 0 clear, re with it set), IM[j] likewise, j = register bits 1..4.
-// Register bit 0 (the "pack bit") is chosen by the host as the bit with the
-// fewest gates in the phase.
+// A thread's 2^RB amplitudes in a phase are NP = 2^(RB-1) packs: RE[j] =
+// (re with register bit 0 clear, re with it set), IM[j] likewise, j = register
+// bits 1..RB-1.  Register bit 0 (the "pack bit") is chosen by the host as the
+// bit with the fewest gates in the phase.
 
 // Gate on register bits (JU + 1, JV + 1): two amplitude pairs per packed
 // instruction.  Same update as rotate<float> (increment formed first).
-template <int JU, int JV>
-__device__ __forceinline__ void gate_packed(u64 (&RE)[16], u64 (&IM)[16], float cm1, float s) {
+template <int NP, int JU, int JV>
+__device__ __forceinline__ void gate_packed(u64 (&RE)[NP], u64 (&IM)[NP], float cm1, float s) {
   const u64 c2 = pack2(cm1, cm1), s2 = pack2(s, s), n2 = pack2(-s, -s);
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
+  for (int j = 0; j < NP; ++j) {
     if (((j >> JU) & 1) == 1 && ((j >> JV) & 1) == 0) {
       const int k = j ^ (1 << JU) ^ (1 << JV);
       const u64 ar = RE[j], ai = IM[j], br = RE[k], bi = IM[k];
@@ -501,10 +531,10 @@ __device__ __forceinline__ void gate_packed(u64 (&RE)[16], u64 (&IM)[16], float 
 
 // Gate on the pack bit and register bit JV + 1: the pair is the high lane of
 // pack j (JV clear) and the low lane of pack j + 2^JV; scalar arithmetic.
-template <int JV>
-__device__ __forceinline__ void gate_packbit(u64 (&RE)[16], u64 (&IM)[16], float cm1, float s) {
+template <int NP, int JV>
+__device__ __forceinline__ void gate_packbit(u64 (&RE)[NP], u64 (&IM)[NP], float cm1, float s) {
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
+  for (int j = 0; j < NP; ++j) {
     if (((j >> JV) & 1) == 0) {
       const int k = j | (1 << JV);
       const float2 rj = unpack2(RE[j]), ij = unpack2(IM[j]), rk = unpack2(RE[k]), ik = unpack2(IM[k]);
@@ -518,23 +548,46 @@ __device__ __forceinline__ void gate_packbit(u64 (&RE)[16], u64 (&IM)[16], float
   }
 }
 
+// combo = index of (ku < kv) among the RB(RB-1)/2 register-bit pairs in
+// lexicographic order: the first RB-1 pair the pack bit (ku = 0).
 __device__ __forceinline__ void gate_combo(u64 (&RE)[16], u64 (&IM)[16], int combo, float cm1, float s) {
   switch (combo) {
-    case 0: gate_packbit<0>(RE, IM, cm1, s); break;
-    case 1: gate_packbit<1>(RE, IM, cm1, s); break;
-    case 2: gate_packbit<2>(RE, IM, cm1, s); break;
-    case 3: gate_packbit<3>(RE, IM, cm1, s); break;
-    case 4: gate_packed<0, 1>(RE, IM, cm1, s); break;
-    case 5: gate_packed<0, 2>(RE, IM, cm1, s); break;
-    case 6: gate_packed<0, 3>(RE, IM, cm1, s); break;
-    case 7: gate_packed<1, 2>(RE, IM, cm1, s); break;
-    case 8: gate_packed<1, 3>(RE, IM, cm1, s); break;
-    default: gate_packed<2, 3>(RE, IM, cm1, s); break;
+    case 0: gate_packbit<16, 0>(RE, IM, cm1, s); break;
+    case 1: gate_packbit<16, 1>(RE, IM, cm1, s); break;
+    case 2: gate_packbit<16, 2>(RE, IM, cm1, s); break;
+    case 3: gate_packbit<16, 3>(RE, IM, cm1, s); break;
+    case 4: gate_packed<16, 0, 1>(RE, IM, cm1, s); break;
+    case 5: gate_packed<16, 0, 2>(RE, IM, cm1, s); break;
+    case 6: gate_packed<16, 0, 3>(RE, IM, cm1, s); break;
+    case 7: gate_packed<16, 1, 2>(RE, IM, cm1, s); break;
+    case 8: gate_packed<16, 1, 3>(RE, IM, cm1, s); break;
+    default: gate_packed<16, 2, 3>(RE, IM, cm1, s); break;
+  }
+}
+__device__ __forceinline__ void gate_combo(u64 (&RE)[32], u64 (&IM)[32], int combo, float cm1, float s) {
+  switch (combo) {
+    case 0: gate_packbit<32, 0>(RE, IM, cm1, s); break;
+    case 1: gate_packbit<32, 1>(RE, IM, cm1, s); break;
+    case 2: gate_packbit<32, 2>(RE, IM, cm1, s); break;
+    case 3: gate_packbit<32, 3>(RE, IM, cm1, s); break;
+    case 4: gate_packbit<32, 4>(RE, IM, cm1, s); break;
+    case 5: gate_packed<32, 0, 1>(RE, IM, cm1, s); break;
+    case 6: gate_packed<32, 0, 2>(RE, IM, cm1, s); break;
+    case 7: gate_packed<32, 0, 3>(RE, IM, cm1, s); break;
+    case 8: gate_packed<32, 0, 4>(RE, IM, cm1, s); break;
+    case 9: gate_packed<32, 1, 2>(RE, IM, cm1, s); break;
+    case 10: gate_packed<32, 1, 3>(RE, IM, cm1, s); break;
+    case 11: gate_packed<32, 1, 4>(RE, IM, cm1, s); break;
+    case 12: gate_packed<32, 2, 3>(RE, IM, cm1, s); break;
+    case 13: gate_packed<32, 2, 4>(RE, IM, cm1, s); break;
+    default: gate_packed<32, 3, 4>(RE, IM, cm1, s); break;
   }
 }
 
-// lowest set bit of a compile-time g in 1..15 (Gray-code walk)
-__host__ __device__ constexpr int ctz4(int g) { return (g & 1) ? 0 : (g & 2) ? 1 : (g & 4) ? 2 : 3; }
+// lowest set bit of a compile-time g in 1..31 (Gray-code walk)
+__host__ __device__ constexpr int ctz5(int g) {
+  return (g & 1) ? 0 : (g & 2) ? 1 : (g & 4) ? 2 : (g & 8) ? 3 : 4;
+}
 
 // 8-byte asynchronous global->shared copy (one amplitude): the swizzle may
 // move an amplitude pair to an odd slot, so 16-byte copies would misalign.
@@ -555,10 +608,14 @@ struct SOp {
 
 }  // namespace sw2
 
-__global__ void __launch_bounds__(512)
+// Register-blocked sweep with RB register bits (2^RB amplitudes per thread,
+// 2^(K-RB) threads per tile).
+template <int RB>
+__global__ void __launch_bounds__(RB == 5 ? 512 : 256)
 sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pdesc,
               const PhaseDesc *__restrict__ phases, const ROp *__restrict__ rops, int M) {
   using sw2::u64;
+  constexpr int NA = 1 << RB, NP = NA / 2;
   const JobPtrs jp = jobs[blockIdx.y];
   float2 *__restrict__ psi = static_cast<float2 *>(jp.psi);
   const GateCoef *__restrict__ coefs = jp.coefs;
@@ -568,10 +625,10 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
   __shared__ uint64_t sH[kMaxK];
   __shared__ uint64_t sQ[kMaxK * kMaxK];
   __shared__ uint64_t sOut;
-  __shared__ uint64_t s_off_hi[64];   // physical offset of the high chunk-index bits
-  __shared__ uint32_t s_slot_st[64];  // slot of the high bits of an output chunk's input index
-  __shared__ uint64_t s_off_amp[32];  // physical offset of the high amplitude-index bits
-  __shared__ uint32_t s_slot_amp[32]; // their shared-memory slot (slot is XOR-linear)
+  __shared__ uint64_t s_off_hi[NP];   // physical offset of the high chunk-index bits
+  __shared__ uint32_t s_slot_st[NP];  // slot of the high bits of an output chunk's input index
+  __shared__ uint64_t s_off_amp[NA];  // physical offset of the high amplitude-index bits
+  __shared__ uint32_t s_slot_amp[NA]; // their shared-memory slot (slot is XOR-linear)
   __shared__ PhaseDesc s_ph[kMaxPassPhases];
   __shared__ sw2::SOp s_op[kMaxPassOps];
   {
@@ -581,7 +638,7 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
   }
   __syncthreads();
   const int K = d.K, tid = threadIdx.x, nt = blockDim.x;
-  const int lognt = 31 - __clz(nt);
+  const int lognt = K - RB;
   const uint64_t base = deposit_bits(blockIdx.x, d.outer_pos, M - K);
   // stage the pass's program: phases, and ops with their coefficients
   for (int i = tid; i < d.nphases; i += nt) s_ph[i] = phases[d.phase0 + i];
@@ -596,13 +653,13 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
     }
     s_op[i] = o;
   }
-  // chunks of two amplitudes (tile bit 0): chunk ch = tid + nt * e covers tile
-  // index 2*ch; tile bits 1..lognt come from tid, the rest from e
-  const int ehi = K - 1 - lognt;  // number of high chunk bits
-  for (int e = tid; e < (1 << ehi); e += nt) {
+  // output chunks of two amplitudes (tile bit 0): chunk ch = tid + nt * e
+  // covers tile index 2*ch; tile bits 1..lognt come from tid, the RB - 1 high
+  // ones from e
+  for (int e = tid; e < NP; e += nt) {
     uint64_t o = 0;
     uint32_t pin = 0;
-    for (int k = 0; k < ehi; ++k) {
+    for (int k = 0; k < RB - 1; ++k) {
       const int q = 1 + lognt + k;
       if ((e >> k) & 1) o |= 1ull << d.tile_pos[q], pin |= 1u << d.perm[q];
     }
@@ -613,12 +670,11 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
   uint32_t pin_lo = 0;
   for (int k = 0; k < lognt; ++k)
     if ((tid >> k) & 1) off_lo |= 1ull << d.tile_pos[1 + k], pin_lo |= 1u << d.perm[1 + k];
-  // amplitude a = tid + nt * e: tile bits 0..lognt-1 from tid, the K - lognt
-  // (= 5) high bits from e
-  constexpr int eamp = 5;
-  for (int e = tid; e < (1 << eamp); e += nt) {
+  // input amplitude a = tid + nt * e: tile bits 0..lognt-1 from tid, the RB
+  // high bits from e
+  for (int e = tid; e < NA; e += nt) {
     uint64_t o = 0;
-    for (int k = 0; k < eamp; ++k)
+    for (int k = 0; k < RB; ++k)
       if ((e >> k) & 1) o |= 1ull << d.tile_pos[lognt + k];
     s_off_amp[e] = o;
     s_slot_amp[e] = sw2::slot((uint32_t)e << lognt);
@@ -634,7 +690,7 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
     const float2 *src = psi + base + off_amp_lo;
     const uint32_t slot_lo = sw2::slot((uint32_t)tid);
 #pragma unroll
-    for (int e = 0; e < (1 << eamp); ++e)
+    for (int e = 0; e < NA; ++e)
       sw2::cp_async8(&tile2[slot_lo ^ s_slot_amp[e]], src + s_off_amp[e]);
   }
   sw2::cp_async_wait_all();
@@ -648,11 +704,11 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
     // slot of this thread's subcube origin (host-precomputed slot of each
     // thread-index bit) and of the register bits
     uint32_t s0 = 0;
-    for (int b = 0; b < K - 5; ++b)
+    for (int b = 0; b < lognt; ++b)
       if ((tid >> b) & 1) s0 ^= ph.tslot[b];
-    uint32_t sm[5];
+    uint32_t sm[RB];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) sm[k] = ph.sm[k];
+    for (int k = 0; k < RB; ++k) sm[k] = ph.sm[k];
     const int o0 = ph.op0 - d.rop0;
     if (ph.nops == 1 && s_op[o0].kind == OP_DIAG) {
       // diagonal phase e^{-i tau D}, amplitude by amplitude in shared memory:
@@ -660,7 +716,7 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
       // outer-outer (sOut), outer-tile (sH) and tile-tile (sQ) parts
       uint32_t t0 = 0;
       for (int k = 0; k < 5; ++k) t0 |= ((uint32_t)(tid >> k) & 1u) << ph.lanes[k];
-      for (int k = 0; k < K - 10; ++k) t0 |= ((uint32_t)(tid >> (5 + k)) & 1u) << ph.warps[k];
+      for (int k = 0; k < lognt - 5; ++k) t0 |= ((uint32_t)(tid >> (5 + k)) & 1u) << ph.warps[k];
       const uint64_t *q = qdiag + (size_t)s_op[o0].arg * M * M;
       if (tid < K) {
         const int pp = d.tile_pos[tid];
@@ -684,7 +740,7 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
       for (int w = tid; w < K * K; w += nt) sQ[w] = q[d.tile_pos[w / K] * M + d.tile_pos[w % K]];
       __syncthreads();
       uint32_t isreg = 0;
-      for (int k = 0; k < 5; ++k) isreg |= 1u << ph.rb[k];
+      for (int k = 0; k < RB; ++k) isreg |= 1u << ph.rb[k];
       // fixed part (tile bits from the thread index) once per thread
       uint64_t th0 = sOut;
       for (int x = 0; x < K; ++x) {
@@ -697,9 +753,9 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
         }
       }
       // field on each register bit from the fixed bits, once per thread
-      uint64_t G[5];
+      uint64_t G[RB];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
+      for (int k = 0; k < RB; ++k) {
         const int rk = ph.rb[k];
         uint64_t g = sH[rk];
         for (int x = 0; x < K; ++x) {
@@ -708,16 +764,16 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
         }
         G[k] = g;
       }
-      for (int i = 0; i < 32; ++i) {
+      for (int i = 0; i < NA; ++i) {
         uint32_t s = s0;
         uint64_t th = th0;
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
+        for (int k = 0; k < RB; ++k) {
           const uint32_t bk = (i >> k) & 1;
           if (bk) s ^= sm[k];
           th += bk ? G[k] : (0ull - G[k]);
 #pragma unroll
-          for (int l = k + 1; l < 5; ++l) {
+          for (int l = k + 1; l < RB; ++l) {
             const uint64_t v = sQ[ph.rb[k] * K + ph.rb[l]];
             th += (bk ^ ((i >> l) & 1)) ? (0ull - v) : v;
           }
@@ -727,14 +783,14 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
       __syncthreads();
       continue;
     }
-    // load the subcube as 16 packs, walking the packs in Gray-code order so
+    // load the subcube as NP packs, walking the packs in Gray-code order so
     // each step changes one register bit (one XOR on the slot)
-    u64 RE[16], IM[16];
+    u64 RE[NP], IM[NP];
     {
       uint32_t s = s0;
 #pragma unroll
-      for (int g = 0; g < 16; ++g) {
-        if (g) s ^= sm[1 + sw2::ctz4(g)];
+      for (int g = 0; g < NP; ++g) {
+        if (g) s ^= sm[1 + sw2::ctz5(g)];
         const int j = g ^ (g >> 1);
         const uint32_t s1 = s ^ sm[0];
         RE[j] = sw2::pack2(tf[2 * s], tf[2 * s1]);
@@ -749,7 +805,7 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
       } else if (cur.kind == OP_REDUCE) {
         int kr = -1;
 #pragma unroll
-        for (int q = 0; q < 5; ++q)
+        for (int q = 0; q < RB; ++q)
           if (ph.rb[q] == d.site_tile) kr = q;
         uint32_t fixed_bit;
         if (d.site_tile < 0) {
@@ -757,11 +813,11 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
         } else {
           uint32_t t0 = 0;
           for (int b = 0; b < 5; ++b) t0 |= ((uint32_t)(tid >> b) & 1u) << ph.lanes[b];
-          for (int b = 0; b < K - 10; ++b) t0 |= ((uint32_t)(tid >> (5 + b)) & 1u) << ph.warps[b];
+          for (int b = 0; b < lognt - 5; ++b) t0 |= ((uint32_t)(tid >> (5 + b)) & 1u) << ph.warps[b];
           fixed_bit = (t0 >> d.site_tile) & 1u;
         }
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < NP; ++j) {
           const float2 pr = sw2::unpack2(sw2::fma2(RE[j], RE[j], sw2::mul2(IM[j], IM[j])));
           if (kr == 0) {
             dn += pr.x;
@@ -778,8 +834,8 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
     {
       uint32_t s = s0;
 #pragma unroll
-      for (int g = 0; g < 16; ++g) {
-        if (g) s ^= sm[1 + sw2::ctz4(g)];
+      for (int g = 0; g < NP; ++g) {
+        if (g) s ^= sm[1 + sw2::ctz5(g)];
         const int j = g ^ (g >> 1);
         const uint32_t s1 = s ^ sm[0];
         const float2 r = sw2::unpack2(RE[j]), i = sw2::unpack2(IM[j]);
@@ -800,7 +856,7 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
     const uint32_t sl0 = sw2::slot(pin_lo), sl1 = sw2::slot(1u << d.perm[0]);
     float2 *dst0 = psi + base + off_lo;
 #pragma unroll 4
-    for (int e = 0; e < (1 << ehi); ++e) {
+    for (int e = 0; e < NP; ++e) {
       const uint32_t s = sl0 ^ s_slot_st[e];
       const float2 v0 = tile2[s], v1 = tile2[s ^ sl1];
       *reinterpret_cast<float4 *>(dst0 + s_off_hi[e]) = make_float4(v0.x, v0.y, v1.x, v1.y);

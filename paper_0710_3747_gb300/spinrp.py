@@ -67,6 +67,7 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             "spinrp_system_num_spins": ([vp], ctypes.c_int),
             "spinrp_system_bonds": ([vp, i32p, ctypes.c_int, ip], ctypes.c_int),
             "spinrp_system_set_tile": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "spinrp_system_set_regbits": ([vp, ctypes.c_int], ctypes.c_int),
             "spinrp_system_plan_info": ([vp, ctypes.c_int, ip, ip, ip], ctypes.c_int),
             "spinrp_system_plan_gates": ([vp, ctypes.c_int, i32p, i32p, ctypes.c_int, ip], ctypes.c_int),
             "spinrp_state_bytes": ([vp, ctypes.c_int, ctypes.c_int64, szp, szp], ctypes.c_int),
@@ -74,6 +75,7 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
                                     ctypes.c_int),
             "spinrp_state_destroy": ([vp], None),
             "spinrp_state_init_random_phase": ([vp, ctypes.c_uint64], ctypes.c_int),
+            "spinrp_state_init_product_phase": ([vp, ctypes.c_uint64], ctypes.c_int),
             "spinrp_state_load": ([vp, dp], ctypes.c_int),
             "spinrp_evolve": ([vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
             "spinrp_series_length": ([vp], ctypes.c_int64),
@@ -167,6 +169,10 @@ class System:
     def set_tile(self, prec, K: int):
         _check(lib().spinrp_system_set_tile(self._h, _PREC[prec], int(K)))
 
+    def set_regbits(self, rb: int):
+        """Register bits per phase of the complex64 kernel (5 or 6; 0 = default)."""
+        _check(lib().spinrp_system_set_regbits(self._h, int(rb)))
+
     def plan_info(self, prec="c64") -> dict:
         s, w, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().spinrp_system_plan_info(self._h, _PREC[prec], ctypes.byref(s), ctypes.byref(w),
@@ -240,6 +246,11 @@ class State:
 
     def init_random_phase(self, seed: int):
         _check(lib().spinrp_state_init_random_phase(self._h, int(seed) & (2**64 - 1)))
+        return self
+
+    def init_product_phase(self, seed: int):
+        """The paper's product (unentangled) random state: M-1 phases."""
+        _check(lib().spinrp_state_init_product_phase(self._h, int(seed) & (2**64 - 1)))
         return self
 
     def load(self, amps: np.ndarray):
@@ -370,6 +381,7 @@ _BATCH_SIG = {
     "spinrp_batch_info": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int)],
                           ctypes.c_int),
     "spinrp_batch_init_random_phase": ([ctypes.c_void_p], ctypes.c_int),
+    "spinrp_batch_init_product_phase": ([ctypes.c_void_p], ctypes.c_int),
     "spinrp_batch_evolve": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
     "spinrp_batch_polarization": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                    ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -416,6 +428,10 @@ class Batch:
 
     def init_random_phase(self):
         _check(_batch_lib().spinrp_batch_init_random_phase(self._h))
+        return self
+
+    def init_product_phase(self):
+        _check(_batch_lib().spinrp_batch_init_product_phase(self._h))
         return self
 
     def evolve(self, dt: float, steps: int, order: int = 2):

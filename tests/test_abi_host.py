@@ -123,8 +123,11 @@ def test_register_phase_programs(name, J, htype, a, K):
 
 
 def test_plan_sweep_counts():
-    # 2x15 ladder, 14-spin tiles sharing 4 low bits: three segments -> four sweeps per step
+    # 2x15 ladder, 13-spin tiles (the default for 2^30 complex64 amplitudes)
+    # sharing 4 low bits: three segments -> four sweeps per step; the same at 14
     s = spinrp.System(W.ladder(15, 1.0, 0.5), spinrp.XY)
+    assert s.plan_info("c64") == {"segments": 3, "sweeps_per_step": 4, "K": 13}
+    s.set_tile("c64", 14)
     assert s.plan_info("c64") == {"segments": 3, "sweeps_per_step": 4, "K": 14}
     # M=20 dipolar star, 14-spin tiles: three segments
     s = spinrp.System(W.star_dipolar(20, 2), spinrp.DIPOLAR)

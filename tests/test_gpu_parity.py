@@ -33,10 +33,12 @@ def _oracle(J, htype, seed, dt, steps, a=None):
     return oracle.run(J, htype, seed, dt, steps, a_generic=a, threads=THREADS)
 
 
-def _gpu(J, htype, seed, dt, steps, prec, a=None, K=None, chunks=None):
+def _gpu(J, htype, seed, dt, steps, prec, a=None, K=None, chunks=None, rb=None):
     s = spinrp.System(J, htype, a)
     if K:
         s.set_tile(prec, K)
+    if rb:
+        s.set_regbits(rb)
     st = spinrp.State(s, prec, series_cap=steps + 1)
     st.init_random_phase(seed)
     for n in (chunks or [steps]):
@@ -113,9 +115,9 @@ def test_multi_tile_plans(kind, K, prec):
     assert np.max(np.abs(amp - psi_w)) <= (1e-12 if prec == "c128" else 2e-6), info
 
 
-@pytest.mark.parametrize("K", [10, 11, 12, 13])
+@pytest.mark.parametrize("rb,K", [(5, 10), (5, 11), (5, 12), (5, 13), (6, 11), (6, 12), (6, 13), (6, 14)])
 @pytest.mark.parametrize("kind", ["star16", "ladder16", "generic15", "chain18"])
-def test_register_blocked_sweeps(kind, K):
+def test_register_blocked_sweeps(kind, rb, K):
     """complex64 tiles of K >= 10 spins run the register-blocked sweep:
     several tiles and segments, relabelling, diagonal phase across tile and
     outer bits."""
@@ -132,7 +134,7 @@ def test_register_blocked_sweeps(kind, K):
         J, ht = W.star_gaussian(15, 3), spinrp.GENERIC
     seed, dt, steps = 11, 0.04, 5
     Pw, Nw, psi_w = _oracle(J, ht, seed, dt, steps, a)
-    Pg, Ng, st = _gpu(J, ht, seed, dt, steps, "c64", a, K=K)
+    Pg, Ng, st = _gpu(J, ht, seed, dt, steps, "c64", a, K=K, rb=rb)
     assert st.system.plan_info("c64")["K"] == K
     assert np.max(np.abs(Pg - Pw)) <= 1e-5
     amp = st.amplitudes()
