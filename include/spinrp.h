@@ -195,11 +195,27 @@ int spinrp_evolve(spinrp_state *st, double dt, int64_t steps, int order);
 /* Number of entries recorded so far (1 after init, +1 per step). */
 int64_t spinrp_series_length(const spinrp_state *st);
 
-/* Copy the recorded polarization series P_{site,1}(t_k), k = 0..len-1, to
- * the host buffer out (min(len, cap) doubles); *n receives len.  Only site 1
- * (the initially polarized spin) is recorded by this build; other sites give
- * SPINRP_EUNSUPPORTED.  Synchronizes the state's stream. */
+/* Copy the recorded polarization series P_{site,1}(t_k), k = 0..len-1 (the
+ * local polarization of spin `site` given spin 1 polarized at t = 0, the
+ * paper's Eq. 2 with m = 1 and P = 2W - 1) to the host buffer out
+ * (min(len, cap) doubles); *n receives len.  Site 1 is always recorded;
+ * sites 2..M need the all-site readout (spinrp_state_set_sites) enabled at
+ * the last init / load, else SPINRP_ESTATE.  Sites outside 1..M give
+ * SPINRP_EINVAL.  Synchronizes the state's stream. */
 int spinrp_polarization(spinrp_state *st, int site, double *out, int64_t cap, int64_t *n);
+
+/* Request (all_sites != 0) or drop the all-site readout from the next
+ * spinrp_state_init_* / spinrp_state_load on: after every Trotter step the
+ * reducing sweep also sums, per block, the weight with each spin up, and a
+ * fixed-order column reduction records P_{q1}(t) = (2 N_up(q) - N)/N of every
+ * spin q (M doubles per entry, in the work buffer spinrp_state_bytes sizes).
+ * No extra pass over the state; one small kernel per step. */
+int spinrp_state_set_sites(spinrp_state *st, int all_sites);
+
+/* All-site series: out[k * M + (q - 1)] = P_{q1}(t_k) for k = 0..min(len,
+ * cap)-1, q = 1..M; *n receives len.  SPINRP_ESTATE unless the all-site
+ * readout was enabled at the last init / load.  Synchronizes. */
+int spinrp_site_series(spinrp_state *st, double *out, int64_t cap, int64_t *n);
 
 /* Same for the norm sum_x |psi_x|^2 after each step. */
 int spinrp_norm_series(spinrp_state *st, double *out, int64_t cap, int64_t *n);

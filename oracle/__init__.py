@@ -257,3 +257,41 @@ def run_product(J: np.ndarray, htype: int, seed: int, dt: float, steps: int, a_g
     n0 = float(np.vdot(psi, psi).real)
     P, nrm = evolve(psi, a, b, dt, steps, site=site, threads=threads)
     return np.concatenate([[p0], P]), np.concatenate([[n0], nrm]), psi
+
+
+def evolve_all_sites(psi: np.ndarray, a: np.ndarray, b: np.ndarray, dt: float, steps: int,
+                     bonds: Iterable[tuple[int, int]] | None = None, threads: int | None = None):
+    """Evolve psi in place; returns (P, norm) with P[n, q-1] the polarization
+    of spin q after step n+1 (every site) and norm[n] the norm."""
+    L = lib()
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.oracle_evolve_all_sites.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_int64, dp, dp,
+                                          ctypes.c_int]
+    L.oracle_evolve_all_sites.restype = ctypes.c_int
+    M = int(np.log2(psi.size))
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    if bonds is None:
+        bonds = canonical_bonds(b)
+    bl = np.ascontiguousarray(np.asarray(list(bonds), dtype=np.int32).reshape(-1, 2))
+    P = np.empty((steps, M), dtype=np.float64)
+    nrm = np.empty(steps, dtype=np.float64)
+    rc = L.oracle_evolve_all_sites(M, _dptr(_as_buf(psi)), _dptr(a), _dptr(b),
+                                   bl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), bl.shape[0],
+                                   float(dt), int(steps), _dptr(P), _dptr(nrm), _threads(threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_evolve_all_sites failed ({rc})")
+    return P, nrm
+
+
+def run_all_sites(J: np.ndarray, htype: int, seed: int, dt: float, steps: int, a_generic=None,
+                  threads: int | None = None, product: bool = False):
+    """Whole job reading out every site: (P[0..steps, 0..M-1], norm[0..steps], psi)."""
+    a, b = couplings(J, htype, a_generic)
+    M = a.shape[0]
+    psi = init_product_phase(M, seed, threads) if product else init_random_phase(M, seed, threads)
+    p0 = np.array([polarization(psi, q) for q in range(1, M + 1)])
+    n0 = float(np.vdot(psi, psi).real)
+    P, nrm = evolve_all_sites(psi, a, b, dt, steps, threads=threads)
+    return np.vstack([p0[None, :], P]), np.concatenate([[n0], nrm]), psi

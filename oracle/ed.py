@@ -76,6 +76,20 @@ class ExactSystem:
         return np.array([np.sum(W2 * np.cos(dE * t)) / N for t in np.atleast_1d(times)])
 
 
+def ensemble_cross_polarization(a: np.ndarray, b: np.ndarray, times, n: int, m: int = 1) -> np.ndarray:
+    """P_{nm}(t) = 2^{-M} Tr[sigma^z_n(t) sigma^z_m] by dense exact diagonalization:
+    sum_{kl} (Z_n)_{kl} (Z_m)_{kl} cos((E_k - E_l) t) / 2^M in the eigenbasis."""
+    ex = ExactSystem(a, b)
+    N = 1 << ex.M
+    x = np.arange(N)
+    zn = ex.V.T @ (np.where((x >> (n - 1)) & 1, 1.0, -1.0)[:, None] * ex.V)
+    zm = ex.V.T @ (np.where((x >> (m - 1)) & 1, 1.0, -1.0)[:, None] * ex.V)
+    W = zn * zm
+    times = np.atleast_1d(np.asarray(times, float))
+    u = np.exp(1j * ex.E[:, None] * times[None, :])
+    return np.real(np.sum(np.conj(u) * (W @ u), axis=0)) / N
+
+
 def sector_ensemble_polarization(a: np.ndarray, b: np.ndarray, times, site: int = 1) -> np.ndarray:
     """Same as ExactSystem.ensemble_polarization, by total-S^z blocks (H and
     sigma^z_site both conserve the number of up spins).  Reaches M ~ 14."""
@@ -134,3 +148,12 @@ def hopping_p11(h: np.ndarray, times) -> np.ndarray:
     times = np.atleast_1d(np.asarray(times, float))
     g = (V[0, :] ** 2)[None, :] * np.exp(-1j * E[None, :] * times[:, None])
     return np.abs(g.sum(axis=1)) ** 2
+
+
+def hopping_pn1(h: np.ndarray, times) -> np.ndarray:
+    """|[e^{-iht}]_{n1}|^2 for every site n (rows: times, columns: n), the
+    free-fermion value of P_{n1}(t) for an XY network with hopping matrix h."""
+    E, V = np.linalg.eigh(h)
+    times = np.atleast_1d(np.asarray(times, float))
+    g = np.einsum("nk,k,tk->tn", V, V[0, :], np.exp(-1j * E[None, :] * times[:, None]))
+    return np.abs(g) ** 2

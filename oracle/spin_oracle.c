@@ -233,37 +233,77 @@ void oracle_site_populations(int M, const double *psi, int site, double *n_up, d
 /* the identity); otherwise its phase table for tau is built once and reused, */
 /* which only memoises values the definition recomputes identically.          */
 /* ------------------------------------------------------------------------ */
+static int has_sz_coupling(int M, const double *a)
+{
+    for (int i = 0; i < M; ++i)
+        for (int j = i + 1; j < M; ++j)
+            if (a[i * M + j] != 0.0) return 1;
+    return 0;
+}
+
+/* One symmetric second-order step: D(tau), forward flip-flops, reversed
+ * flip-flops, D(tau); ph is the D(tau) phase table or NULL when D = 0. */
+static void trotter_step(int M, double *psi, const double *ph, const double *b, const int32_t *bonds,
+                         int nbonds, double tau, int nthreads)
+{
+    if (ph) oracle_apply_table(M, psi, ph, nthreads);
+    for (int k = 0; k < nbonds; ++k) {
+        const int i = bonds[2 * k], j = bonds[2 * k + 1];
+        oracle_flipflop(M, psi, i, j, b[i * M + j], tau, nthreads);
+    }
+    for (int k = nbonds - 1; k >= 0; --k) {
+        const int i = bonds[2 * k], j = bonds[2 * k + 1];
+        oracle_flipflop(M, psi, i, j, b[i * M + j], tau, nthreads);
+    }
+    if (ph) oracle_apply_table(M, psi, ph, nthreads);
+}
+
 int oracle_evolve(int M, double *psi, const double *a, const double *b, const int32_t *bonds,
                   int nbonds, double dt, int64_t steps, int site, double *P, double *norm,
                   int nthreads)
 {
     if (M < 2 || site < 1 || site > M || nbonds < 0) return 1;
     const double tau = 0.5 * dt;
-    int has_diag = 0;
-    for (int i = 0; i < M; ++i)
-        for (int j = i + 1; j < M; ++j)
-            if (a[i * M + j] != 0.0) has_diag = 1;
     double *ph = NULL;
-    if (has_diag) {
+    if (has_sz_coupling(M, a)) {
         ph = (double *)malloc(sizeof(double) * 2 * ((size_t)1 << M));
         if (!ph) return 2;
         oracle_diag_table(M, a, tau, ph, nthreads);
     }
     for (int64_t n = 0; n < steps; ++n) {
-        if (has_diag) oracle_apply_table(M, psi, ph, nthreads);
-        for (int k = 0; k < nbonds; ++k) {
-            const int i = bonds[2 * k], j = bonds[2 * k + 1];
-            oracle_flipflop(M, psi, i, j, b[i * M + j], tau, nthreads);
-        }
-        for (int k = nbonds - 1; k >= 0; --k) {
-            const int i = bonds[2 * k], j = bonds[2 * k + 1];
-            oracle_flipflop(M, psi, i, j, b[i * M + j], tau, nthreads);
-        }
-        if (has_diag) oracle_apply_table(M, psi, ph, nthreads);
+        trotter_step(M, psi, ph, b, bonds, nbonds, tau, nthreads);
         double up, dn;
         oracle_site_populations(M, psi, site, &up, &dn, nthreads);
         if (P) P[n] = (up - dn) / (up + dn);
         if (norm) norm[n] = up + dn;
+    }
+    free(ph);
+    return 0;
+}
+
+/* Same evolution, reading out every site: after step n, Pall[n*M + q-1] =
+ * (N_up - N_dn)/(N_up + N_dn) of spin q (q = 1..M), the local polarizations
+ * P_{q1}(t) of the paper's Eq. 2 with m = 1, and norm[n] = N_up + N_dn. */
+int oracle_evolve_all_sites(int M, double *psi, const double *a, const double *b,
+                            const int32_t *bonds, int nbonds, double dt, int64_t steps, double *Pall,
+                            double *norm, int nthreads)
+{
+    if (M < 2 || nbonds < 0) return 1;
+    const double tau = 0.5 * dt;
+    double *ph = NULL;
+    if (has_sz_coupling(M, a)) {
+        ph = (double *)malloc(sizeof(double) * 2 * ((size_t)1 << M));
+        if (!ph) return 2;
+        oracle_diag_table(M, a, tau, ph, nthreads);
+    }
+    for (int64_t n = 0; n < steps; ++n) {
+        trotter_step(M, psi, ph, b, bonds, nbonds, tau, nthreads);
+        for (int q = 1; q <= M; ++q) {
+            double up, dn;
+            oracle_site_populations(M, psi, q, &up, &dn, nthreads);
+            Pall[n * M + (q - 1)] = (up - dn) / (up + dn);
+            if (q == 1 && norm) norm[n] = up + dn;
+        }
     }
     free(ph);
     return 0;

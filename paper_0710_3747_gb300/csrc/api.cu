@@ -214,7 +214,7 @@ struct PassSet {
 
 struct Layout {  // byte offsets inside the work buffer
   size_t series, partials, ticket, job, coefs, bvals, adiag, qdiag, passes, ops, phases, rops, stage,
-      stage_idx, total;
+      stage_idx, psites, site_series, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -241,6 +241,9 @@ struct spinrp_state {
   // device views
   double *series = nullptr;
   double2 *partials = nullptr;
+  double *psites = nullptr, *site_series = nullptr;
+  bool sites_req = false;     // all-site readout requested for the next init / load
+  bool sites = false;         // all-site readout active for the current series
   unsigned *ticket = nullptr;
   GateCoef *coefs = nullptr;
   double *d_bvals = nullptr, *d_a = nullptr;
@@ -316,6 +319,8 @@ static void build_passes(const Plan &p, bool has_diag, PassSet *ps) {
       d.perm[qo] = (uint8_t)qi;
       if (qi != qo) d.relabel = 1;
     }
+    for (int qo = 0; qo < K; ++qo) d.tile_spin[qo] = (uint8_t)in_spin[tpos[qo]];
+    for (int o = 0; o < no; ++o) d.outer_spin[o] = (uint8_t)in_spin[d.outer_pos[o]];
     d.site_pos = Lin[0];
     d.site_tile = -1;
     for (int q = 0; q < K; ++q)
@@ -434,6 +439,8 @@ static Layout work_layout(int M, int nb, int64_t cap, const PassSet &ps, int max
   L.rops = o, o = align256(o + sizeof(ROp) * std::max<size_t>(ps.rops.size(), 1));
   L.stage = o, o = align256(o + sizeof(double2) * kStage);
   L.stage_idx = o, o = align256(o + sizeof(int64_t) * kStage);
+  L.psites = o, o = align256(o + sizeof(double) * (M + 1) * (size_t)max_blocks);
+  L.site_series = o, o = align256(o + sizeof(double) * M * (size_t)std::max<int64_t>(cap, 1));
   L.total = o;
   return L;
 }
@@ -623,12 +630,15 @@ template <typename R>
 static int set_smem_limits() {
   // the widest tile of this precision (2^14 c64 or 2^13 c128 = 128 KiB)
   const int kmax = sizeof(R) == 4 ? 14 : 13;
-  CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(typename CT<R>::T) << kmax)));
+  const int wide = (int)(sizeof(typename CT<R>::T) << kmax);
+  CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, wide));
+  CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, wide));
   if (sizeof(R) == 4)
   {
-    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
-    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
+    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<5, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
+    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
+    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<5, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
+    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
   }
   return SPINRP_OK;
 }
@@ -703,9 +713,11 @@ extern "C" int spinrp_state_create(const spinrp_system *sys, int prec, void *str
   st->v2 = st->ps.phased;
   st->stage = (double2 *)(w + st->lay.stage);
   st->stage_idx = (int64_t *)(w + st->lay.stage_idx);
+  st->psites = (double *)(w + st->lay.psites);
+  st->site_series = (double *)(w + st->lay.site_series);
   st->d_step = (int64_t *)(w + st->lay.ticket + 64);
   st->d_job = (JobPtrs *)(w + st->lay.job);
-  JobPtrs hj;
+  JobPtrs hj{};
   hj.psi = st->psi;
   hj.coefs = st->coefs;
   hj.qdiag = st->qdiag;
@@ -715,6 +727,8 @@ extern "C" int spinrp_state_create(const spinrp_system *sys, int prec, void *str
   hj.series = st->series;
   hj.bvals = st->d_bvals;
   hj.a = st->d_a;
+  hj.psites = st->psites;
+  hj.site_series = st->site_series;
 
   auto up = [&](void *dst, const void *src, size_t n) -> cudaError_t {
     if (n == 0) return cudaSuccess;
@@ -755,8 +769,34 @@ static LayoutArg layout_arg(const spinrp_state *st) {
   return la;
 }
 
+// Apply the requested readout mode at the start of a series; cached graphs
+// hold the launches of the previous mode and are dropped when it changes.
+static void begin_series(spinrp_state *st) {
+  if (st->sites != st->sites_req) {
+    for (cudaGraphExec_t &g : st->graphs)
+      if (g) cudaGraphExecDestroy(g), g = nullptr;
+    st->sites = st->sites_req;
+  }
+}
+
+// All-site entry 0 (after init / load recorded entry 0 of the main series).
+static int record_sites0(spinrp_state *st) {
+  if (!st->sites) return SPINRP_OK;
+  const int blocks = init_blocks(st->M);
+  g_launches += 2;
+  if (st->prec == SPINRP_C64)
+    state_sites_kernel<float><<<blocks, 256, 0, st->stream>>>(st->d_job, st->M, layout_arg(st));
+  else
+    state_sites_kernel<double><<<blocks, 256, 0, st->stream>>>(st->d_job, st->M, layout_arg(st));
+  CUDA_TRY(cudaGetLastError());
+  sites_finalize_kernel<<<st->M, 256, 0, st->stream>>>(st->d_job, st->M, blocks);
+  CUDA_TRY(cudaGetLastError());
+  return SPINRP_OK;
+}
+
 static int state_init(spinrp_state *st, uint64_t seed, int kind) {
   if (!st) return fail(SPINRP_EINVAL, "init: state is NULL");
+  begin_series(st);
   const int blocks = init_blocks(st->M);
   prof_mark(st, SPINRP_KERNEL_INIT);
   ++g_launches;
@@ -767,6 +807,8 @@ static int state_init(spinrp_state *st, uint64_t seed, int kind) {
     init_kernel<double><<<blocks, 256, 0, st->stream>>>(st->d_job, st->M, layout_arg(st), seed, nullptr,
                                                         kind);
   CUDA_TRY(cudaGetLastError());
+  int rc = record_sites0(st);
+  if (rc) return rc;
   prof_mark(st, SPINRP_KERNEL_INIT);
   st->len = 1;
   st->ready = true;
@@ -790,6 +832,7 @@ static int64_t to_physical(const spinrp_state *st, int64_t x) {
 
 extern "C" int spinrp_state_load(spinrp_state *st, const double *amps) {
   if (!st || !amps) return fail(SPINRP_EINVAL, "load: bad argument");
+  begin_series(st);
   const int64_t N = int64_t(1) << st->M;
   std::vector<int64_t> idx;
   for (int64_t k0 = 0; k0 < N; k0 += kStage) {
@@ -815,6 +858,8 @@ extern "C" int spinrp_state_load(spinrp_state *st, const double *amps) {
   else
     observe_kernel<double><<<blocks, 256, 0, st->stream>>>(st->d_job, st->M, st->plan.pos[0]);
   CUDA_TRY(cudaGetLastError());
+  int rc = record_sites0(st);
+  if (rc) return rc;
   CUDA_TRY(cudaStreamSynchronize(st->stream));
   st->len = 1;
   st->ready = true;
@@ -870,6 +915,7 @@ struct LaunchCtx {
   const JobPtrs *jobs = nullptr;
   int njobs = 1;
   int rb = 5;                    // register bits of the register-blocked kernel
+  int sites = 0;                 // all-site readout after every reducing sweep
   spinrp_state *prof = nullptr;  // state whose profiling marks to record, if any
 };
 
@@ -887,16 +933,27 @@ static int launch_pass(const LaunchCtx &c, int pass, cudaStream_t stream, bool l
   }
   if (sizeof(R) == 4 && c.v2)
   {
-    if (c.rb == 6)
-      sweep2_kernel<6><<<grid, 1 << (K - 6), size_t(8) << K, stream>>>(c.jobs, c.passes + pass, c.phases,
-                                                                        c.rops, c.M);
+    const size_t sm2 = size_t(8) << K;
+    const PassDesc *pd = c.passes + pass;
+    if (c.rb == 6 && c.sites)
+      sweep2_kernel<6, true><<<grid, 1 << (K - 6), sm2, stream>>>(c.jobs, pd, c.phases, c.rops, c.M);
+    else if (c.rb == 6)
+      sweep2_kernel<6, false><<<grid, 1 << (K - 6), sm2, stream>>>(c.jobs, pd, c.phases, c.rops, c.M);
+    else if (c.sites)
+      sweep2_kernel<5, true><<<grid, 1 << (K - 5), sm2, stream>>>(c.jobs, pd, c.phases, c.rops, c.M);
     else
-      sweep2_kernel<5><<<grid, 1 << (K - 5), size_t(8) << K, stream>>>(c.jobs, c.passes + pass, c.phases,
-                                                                        c.rops, c.M);
+      sweep2_kernel<5, false><<<grid, 1 << (K - 5), sm2, stream>>>(c.jobs, pd, c.phases, c.rops, c.M);
   }
+  else if (c.sites)
+    sweep_kernel<R, true><<<grid, nt, smem, stream>>>(c.jobs, c.passes + pass, c.ops, c.M);
   else
-    sweep_kernel<R><<<grid, nt, smem, stream>>>(c.jobs, c.passes + pass, c.ops, c.M);
+    sweep_kernel<R, false><<<grid, nt, smem, stream>>>(c.jobs, c.passes + pass, c.ops, c.M);
   CUDA_TRY(cudaGetLastError());
+  if (c.sites && c.ps->desc[pass].has_reduce) {
+    if (live) ++g_launches;
+    sites_finalize_kernel<<<dim3(c.M, c.njobs), 256, 0, stream>>>(c.jobs, c.M, 1 << (c.M - K));
+    CUDA_TRY(cudaGetLastError());
+  }
   if (live && c.prof) prof_mark(c.prof, SPINRP_KERNEL_SWEEP);
   return SPINRP_OK;
 }
@@ -1031,6 +1088,7 @@ static LaunchCtx state_ctx(spinrp_state *st) {
   c.K = st->plan.K;
   c.v2 = st->v2;
   c.rb = st->ps.rb;
+  c.sites = st->sites ? 1 : 0;
   c.segments = st->plan.segments();
   c.sweeps_per_step = st->plan.sweeps_per_step();
   c.ps = &st->ps;
@@ -1095,10 +1153,43 @@ static int copy_series(spinrp_state *st, int which, double *out, int64_t cap, in
   return SPINRP_OK;
 }
 
+extern "C" int spinrp_state_set_sites(spinrp_state *st, int all_sites) {
+  if (!st) return fail(SPINRP_EINVAL, "set_sites: state is NULL");
+  st->sites_req = all_sites != 0;
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_site_series(spinrp_state *st, double *out, int64_t cap, int64_t *n) {
+  if (!st || !n || (cap > 0 && !out)) return fail(SPINRP_EINVAL, "site_series: bad argument");
+  if (!st->ready || !st->sites)
+    return fail(SPINRP_ESTATE, "site_series: all-site readout was not enabled at the last init / load");
+  *n = st->len;
+  const int64_t m = std::min(cap, st->len);
+  if (m <= 0) return SPINRP_OK;
+  CUDA_TRY(cudaMemcpyAsync(out, st->site_series, sizeof(double) * st->M * m, cudaMemcpyDeviceToHost,
+                           st->stream));
+  st->d2h += (int64_t)sizeof(double) * st->M * m;
+  CUDA_TRY(cudaStreamSynchronize(st->stream));
+  return SPINRP_OK;
+}
+
 extern "C" int spinrp_polarization(spinrp_state *st, int site, double *out, int64_t cap, int64_t *n) {
-  if (st && site != 1)
-    return fail(SPINRP_EUNSUPPORTED, "polarization: only site 1 is recorded (got %d)", site);
-  return copy_series(st, 0, out, cap, n);
+  if (!st) return fail(SPINRP_EINVAL, "polarization: state is NULL");
+  if (site < 1 || site > st->M) return fail(SPINRP_EINVAL, "polarization: site %d outside 1..%d", site, st->M);
+  if (site == 1) return copy_series(st, 0, out, cap, n);
+  if (!n || (cap > 0 && !out)) return fail(SPINRP_EINVAL, "polarization: bad argument");
+  if (!st->ready || !st->sites)
+    return fail(SPINRP_ESTATE, "polarization: site %d needs the all-site readout (spinrp_state_set_sites)", site);
+  *n = st->len;
+  const int64_t m = std::min(cap, st->len);
+  if (m <= 0) return SPINRP_OK;
+  std::vector<double> buf((size_t)st->M * m);
+  CUDA_TRY(cudaMemcpyAsync(buf.data(), st->site_series, sizeof(double) * buf.size(), cudaMemcpyDeviceToHost,
+                           st->stream));
+  st->d2h += (int64_t)sizeof(double) * buf.size();
+  CUDA_TRY(cudaStreamSynchronize(st->stream));
+  for (int64_t k = 0; k < m; ++k) out[k] = buf[k * st->M + (site - 1)];
+  return SPINRP_OK;
 }
 
 extern "C" int spinrp_norm_series(spinrp_state *st, double *out, int64_t cap, int64_t *n) {

@@ -41,6 +41,8 @@ struct PassDesc {
   uint8_t tile_pos[kMaxK];
   uint8_t outer_pos[kMaxM];
   uint8_t perm[kMaxK];  // store: output tile bit q takes the amplitude bit of input tile bit perm[q]
+  uint8_t tile_spin[kMaxK];   // logical spin (0-based) at each tile bit, input layout
+  uint8_t outer_spin[kMaxM];  // logical spin at each outer bit, input layout
   int32_t phase0;       // register-blocked program (complex64 path): first phase
   int32_t nphases;      //   and number of phases,
   int32_t rop0;         //   first op
@@ -99,14 +101,20 @@ struct JobPtrs {
   double *series;          // (P, norm) per recorded step
   const double *bvals;     // flip-flop coupling of each bond (for the gate tables)
   const double *a;         // M * M S^zS^z couplings, logical indexing (for the phase tables)
+  double *psites;          // all-site readout: (M + 1) columns of per-block sums, column 0 the
+                           // norm, column 1 + q the weight with spin q up (q logical, 0-based);
+                           // nullptr when only spin 1 is read out
+  double *site_series;     // all-site readout: P of spin q at entry k in site_series[k * M + q]
 };
 
-// Gate coefficients of exp(-i theta sigma_x) on a flip-flop pair, theta = b tau/2,
-// stored as (cos theta - 1, sin theta) so that small rotations keep their
-// relative precision: x' = x + cm1 x - i s y.
+// Gate coefficients of exp(-i theta sigma_x) on a flip-flop pair, theta = b tau/2.
+// FP64: (cos theta - 1, sin theta), so that small rotations keep their
+// relative precision: x' = x + cm1 x - i s y.  FP32: (tan theta/2, sin theta)
+// of the three-shear form of the two real plane rotations the gate is made of
+// (see shear_rotate).
 struct GateCoef {
   double cm1, s;
-  float cm1f, sf;
+  float tf, sft;
 };
 
 // ---------------------------------------------------------------------------

@@ -136,6 +136,113 @@ __device__ void reduce_finalize(double up, double dn, const JobPtrs &jp, bool re
 }
 
 // ---------------------------------------------------------------------------
+// All-site readout (P_{q1}(t) for every spin q).  A reducing sweep leaves per
+// block, per tile bit, the weight with that bit up (and the block's norm);
+// write_site_partials turns them into per-spin columns and
+// sites_finalize_kernel sums the columns over blocks in a fixed order.
+// ---------------------------------------------------------------------------
+constexpr int kSiteSlots = kMaxK + 1;  // tile bits 0..kMaxK-1, slot kMaxK = norm
+constexpr int kMaxWarps = 16;
+
+// Warp-sum v (in the thread's precision) and park it at s_w[warp][slot].
+template <typename R>
+__device__ __forceinline__ void warp_site_sum(R v, int slot, double *s_w) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) s_w[(threadIdx.x >> 5) * kSiteSlots + slot] = (double)v;
+}
+
+// After a __syncthreads that follows every warp_site_sum: block sums over the
+// warps in order, written as this block's row of the (M + 1) columns.
+__device__ void write_site_partials(const PassDesc &d, int M, uint64_t base, const double *s_w,
+                                    double *psites) {
+  const int nw = (blockDim.x + 31) >> 5, K = d.K;
+  const size_t nblk = gridDim.x, blk = blockIdx.x;
+  for (int i = threadIdx.x; i <= M; i += blockDim.x) {
+    double norm = 0.0;
+    for (int w = 0; w < nw; ++w) norm += s_w[w * kSiteSlots + kMaxK];
+    double v;
+    int col;
+    if (i < K) {
+      v = 0.0;
+      for (int w = 0; w < nw; ++w) v += s_w[w * kSiteSlots + i];
+      col = 1 + d.tile_spin[i];
+    } else if (i < M) {
+      const int o = i - K;
+      v = ((base >> d.outer_pos[o]) & 1ull) ? norm : 0.0;
+      col = 1 + d.outer_spin[o];
+    } else {
+      v = norm;
+      col = 0;
+    }
+    psites[col * nblk + blk] = v;
+  }
+}
+
+// Whole-state scan (after init or load): per block, the norm and the weight
+// with each spin up, as the same (M + 1) columns.
+template <typename R>
+__global__ void __launch_bounds__(256)
+state_sites_kernel(const JobPtrs *__restrict__ jobs, int M, LayoutArg lay) {
+  const JobPtrs jp = jobs[blockIdx.y];
+  const typename CT<R>::T *__restrict__ psi = static_cast<const typename CT<R>::T *>(jp.psi);
+  const uint64_t N = 1ull << M;
+  R up[kMaxM], norm = 0;
+#pragma unroll
+  for (int p = 0; p < kMaxM; ++p) up[p] = 0;
+  for (uint64_t y = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; y < N;
+       y += (uint64_t)gridDim.x * blockDim.x) {
+    const typename CT<R>::T v = psi[y];
+    const R pr = v.x * v.x + v.y * v.y;
+    norm += pr;
+#pragma unroll
+    for (int p = 0; p < kMaxM; ++p)
+      if (p < M && ((y >> p) & 1ull)) up[p] += pr;
+  }
+  __shared__ double s_w[kMaxWarps * (kMaxM + 1)];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int p = 0; p <= kMaxM; ++p) {
+    R v = p < kMaxM ? up[p] : norm;
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_w[warp * (kMaxM + 1) + p] = (double)v;
+  }
+  __syncthreads();
+  const size_t nblk = gridDim.x, blk = blockIdx.x;
+  for (int i = threadIdx.x; i <= M; i += blockDim.x) {
+    const int slot = i < M ? i : kMaxM;
+    double v = 0.0;
+    for (int w = 0; w < nw; ++w) v += s_w[w * (kMaxM + 1) + slot];
+    const int col = i < M ? 1 + lay.logical_of[i] : 0;
+    jp.psites[col * nblk + blk] = v;
+  }
+}
+
+// P of every spin for the entry the preceding reduction recorded (slot
+// *step - 1): block q sums columns 0 and 1 + q over the nblk block rows in a
+// fixed order, P_q = (2 N_up - N) / N.
+__global__ void __launch_bounds__(256)
+sites_finalize_kernel(const JobPtrs *__restrict__ jobs, int M, int nblk) {
+  const JobPtrs jp = jobs[blockIdx.y];
+  const int q = blockIdx.x;
+  const double *__restrict__ c0 = jp.psites;
+  const double *__restrict__ cq = jp.psites + (size_t)(1 + q) * nblk;
+  double n = 0.0, u = 0.0;
+  for (int r = threadIdx.x; r < nblk; r += blockDim.x) n += c0[r], u += cq[r];
+  __shared__ double sn[256], su[256];
+  sn[threadIdx.x] = n;
+  su[threadIdx.x] = u;
+  __syncthreads();
+  for (int h = 128; h; h >>= 1) {
+    if (threadIdx.x < h) sn[threadIdx.x] += sn[threadIdx.x + h], su[threadIdx.x] += su[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int64_t slot = *jp.step - 1;
+    jp.site_series[slot * M + q] = (2.0 * su[0] - sn[0]) / sn[0];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Random-phase initial state.
 // ---------------------------------------------------------------------------
 // kind INIT_ENTANGLED: an independent phase per basis state of spins 2..M.
@@ -223,20 +330,21 @@ __global__ void coef_kernel(const JobPtrs *__restrict__ jobs, int nb, double dt)
   GateCoef g;
   g.cm1 = cm1;
   g.s = s;
-  // FP32 pair: among +-2 ulps of the rounded values, the one whose rotation is
-  // closest to unitary, |(1+c)^2 + s^2 - 1| = |2c + c^2 + s^2|.
-  const float c0 = (float)cm1, s0 = (float)s;
-  float bc = c0, bs = s0;
-  double best = fabs(2.0 * (double)c0 + (double)c0 * c0 + (double)s0 * s0);
-  for (int dc = -2; dc <= 2; ++dc)
+  // FP32 shear pair: among +-2 ulps of the rounded values, the one closest to a
+  // rotation, |s (1 + t^2) - 2 t| (zero exactly when s = sin 2 atan t)
+  const double tt = tan(0.5 * th);
+  const float t0 = (float)tt, s1 = (float)s;
+  float bt = t0, bs2 = s1;
+  double best2 = fabs((double)s1 * (1.0 + (double)t0 * t0) - 2.0 * (double)t0);
+  for (int dtt = -2; dtt <= 2; ++dtt)
     for (int ds = -2; ds <= 2; ++ds) {
-      const float cf = (c0 == 0.0f) ? c0 : __int_as_float(__float_as_int(c0) + dc);
-      const float sf = (s0 == 0.0f) ? s0 : __int_as_float(__float_as_int(s0) + ds);
-      const double def = fabs(2.0 * (double)cf + (double)cf * cf + (double)sf * sf);
-      if (def < best) best = def, bc = cf, bs = sf;
+      const float tf = (t0 == 0.0f) ? t0 : __int_as_float(__float_as_int(t0) + dtt);
+      const float sf = (s1 == 0.0f) ? s1 : __int_as_float(__float_as_int(s1) + ds);
+      const double def = fabs((double)sf * (1.0 + (double)tf * tf) - 2.0 * (double)tf);
+      if (def < best2) best2 = def, bt = tf, bs2 = sf;
     }
-  g.cm1f = bc;
-  g.sf = bs;
+  g.tf = bt;
+  g.sft = bs2;
   out[k] = g;
 }
 
@@ -265,22 +373,24 @@ __global__ void diag_kernel(const JobPtrs *__restrict__ jobs, LayoutArg lay, int
 // One sweep.  Each block owns one tile: it loads the tile's 2^K amplitudes
 // into shared memory, applies the pass's ops in order and stores the tile.
 // ---------------------------------------------------------------------------
-// a' = a + cm1 a - i s b ; b' = b + cm1 b - i s a.
-// FP32: the small increment d = cm1 a - i s b is formed first and added to a
-// with a single rounding; rounding a(1 + cm1) on its own first biases |a|^2
-// upwards (measured: the norm grows ~1e-9 per gate application, linearly).
-template <typename R>
-__device__ __forceinline__ void rotate(typename CT<R>::T &a, typename CT<R>::T &b, R cm1, R s);
-
-template <>
-__device__ __forceinline__ void rotate<float>(float2 &a, float2 &b, float cm1, float s) {
-  const float ax = a.x, ay = a.y, bx = b.x, by = b.y;
-  a.x = ax + fmaf(cm1, ax, s * by);
-  a.y = ay + fmaf(cm1, ay, -s * bx);
-  b.x = bx + fmaf(cm1, bx, s * ay);
-  b.y = by + fmaf(cm1, by, -s * ax);
+// FP32 gate as two real plane rotations: exp(-i theta sigma_x) maps
+// (Re a, Im b) and (Re b, Im a) each by [[c, s], [-s, c]], c = cos theta,
+// s = sin theta, and each rotation is three shears x += t y, y -= s x,
+// x += t y with t = tan(theta/2): three FMAs per plane.  A shear has
+// determinant one whatever t and s are rounded to, so rounding leaves no
+// uniform gain or loss of norm.
+__device__ __forceinline__ void shear_rotate(float2 &a, float2 &b, float t, float s) {
+  float x = fmaf(t, b.y, a.x);
+  b.y = fmaf(-s, x, b.y);
+  a.x = fmaf(t, b.y, x);
+  x = fmaf(t, a.y, b.x);
+  a.y = fmaf(-s, x, a.y);
+  b.x = fmaf(t, a.y, x);
 }
 
+// FP64 gate: a' = a + cm1 a - i s b ; b' = b + cm1 b - i s a (cm1 = cos - 1).
+template <typename R>
+__device__ __forceinline__ void rotate(typename CT<R>::T &a, typename CT<R>::T &b, R cm1, R s);
 template <>
 __device__ __forceinline__ void rotate<double>(double2 &a, double2 &b, double cm1, double s) {
   const double ax = a.x, ay = a.y, bx = b.x, by = b.y;
@@ -290,7 +400,7 @@ __device__ __forceinline__ void rotate<double>(double2 &a, double2 &b, double cm
   b.y = fma(-s, ax, fma(cm1, by, by));
 }
 
-template <typename R>
+template <typename R, bool SITES>
 __global__ void __launch_bounds__(512)
 sweep_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pdesc,
              const Op *__restrict__ ops, int M) {
@@ -305,6 +415,7 @@ sweep_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pdes
   __shared__ uint64_t sH[kMaxK];
   __shared__ uint64_t sQ[kMaxK * kMaxK];
   __shared__ uint64_t sOut;
+  __shared__ double s_w[SITES ? kMaxWarps * kSiteSlots : 1];
   {
     const int nwords = (int)(sizeof(PassDesc) / 4);
     for (int w = threadIdx.x; w < nwords; w += blockDim.x)
@@ -331,14 +442,15 @@ sweep_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pdes
     const Op op = ops[d.op0 + k];
     if (op.kind == OP_GATE) {
       const GateCoef g = coefs[op.coef];
-      const R cm1 = sizeof(R) == 8 ? (R)g.cm1 : (R)g.cm1f;
-      const R s = sizeof(R) == 8 ? (R)g.s : (R)g.sf;
+      const R c1 = sizeof(R) == 8 ? (R)g.cm1 : (R)g.tf;
+      const R s = sizeof(R) == 8 ? (R)g.s : (R)g.sft;
       const int lo = op.u < op.v ? op.u : op.v, hi = op.u < op.v ? op.v : op.u;
       const uint32_t bu = 1u << op.u, bv = 1u << op.v;
       for (uint32_t p = tid; p < (T >> 2); p += nt) {
         const uint32_t t0 = insert_zero(insert_zero(p, lo), hi);
         C a = tile[t0 | bu], b = tile[t0 | bv];
-        rotate<R>(a, b, cm1, s);
+        if constexpr (sizeof(R) == 8) rotate<R>(a, b, c1, s);
+        else shear_rotate(a, b, c1, s);
         tile[t0 | bu] = a;
         tile[t0 | bv] = b;
       }
@@ -396,6 +508,9 @@ sweep_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pdes
       }
       __syncthreads();
     } else if (op.kind == OP_REDUCE) {
+      R tsum = 0, uhi[kMaxK];
+#pragma unroll
+      for (int q = 0; q < kMaxK; ++q) uhi[q] = 0;
       for (uint32_t t = tid; t < T; t += nt) {
         const C a = tile[t];
         const R pr = a.x * a.x + a.y * a.y;
@@ -403,6 +518,19 @@ sweep_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pdes
                                               : ((base >> d.site_pos) & 1ull);
         if (bit) up += pr;
         else dn += pr;
+        if constexpr (SITES) {
+          tsum += pr;
+#pragma unroll
+          for (int q = 0; q < kMaxK; ++q)
+            if (q >= L && q < K && ((t >> q) & 1u)) uhi[q] += pr;
+        }
+      }
+      if constexpr (SITES) {
+        // tile bits below L come from the thread index: the thread's whole sum
+#pragma unroll
+        for (int q = 0; q < kMaxK; ++q)
+          warp_site_sum<R>(q < L ? (((tid >> q) & 1) ? tsum : (R)0) : uhi[q], q, s_w);
+        warp_site_sum<R>(tsum, kMaxK, s_w);
       }
       __syncthreads();  // later ops overwrite the tile
     }
@@ -417,6 +545,8 @@ sweep_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pdes
       psi[base + offset(t)] = tile[ti];
     }
   }
+  if constexpr (SITES)
+    if (d.has_reduce) write_site_partials(d, M, base, s_w, jp.psites);
   if (d.has_reduce) reduce_finalize((double)up, (double)dn, jp, false);
 }
 
@@ -512,19 +642,21 @@ __device__ __forceinline__ float2 unpack2(u64 v) {
 // bit with the fewest gates in the phase.
 
 // Gate on register bits (JU + 1, JV + 1): two amplitude pairs per packed
-// instruction.  Same update as rotate<float> (increment formed first).
+// instruction, same three-shear update as shear_rotate.
 template <int NP, int JU, int JV>
-__device__ __forceinline__ void gate_packed(u64 (&RE)[NP], u64 (&IM)[NP], float cm1, float s) {
-  const u64 c2 = pack2(cm1, cm1), s2 = pack2(s, s), n2 = pack2(-s, -s);
+__device__ __forceinline__ void gate_packed(u64 (&RE)[NP], u64 (&IM)[NP], float t, float s) {
+  const u64 t2 = pack2(t, t), n2 = pack2(-s, -s);
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
     if (((j >> JU) & 1) == 1 && ((j >> JV) & 1) == 0) {
       const int k = j ^ (1 << JU) ^ (1 << JV);
-      const u64 ar = RE[j], ai = IM[j], br = RE[k], bi = IM[k];
-      RE[j] = add2(ar, fma2(c2, ar, mul2(s2, bi)));
-      IM[j] = add2(ai, fma2(c2, ai, mul2(n2, br)));
-      RE[k] = add2(br, fma2(c2, br, mul2(s2, ai)));
-      IM[k] = add2(bi, fma2(c2, bi, mul2(n2, ar)));
+      // plane (Re a, Im b) = (RE[j], IM[k]); plane (Re b, Im a) = (RE[k], IM[j])
+      u64 x = fma2(t2, IM[k], RE[j]);
+      IM[k] = fma2(n2, x, IM[k]);
+      RE[j] = fma2(t2, IM[k], x);
+      x = fma2(t2, IM[j], RE[k]);
+      IM[j] = fma2(n2, x, IM[j]);
+      RE[k] = fma2(t2, IM[j], x);
     }
   }
 }
@@ -532,14 +664,14 @@ __device__ __forceinline__ void gate_packed(u64 (&RE)[NP], u64 (&IM)[NP], float 
 // Gate on the pack bit and register bit JV + 1: the pair is the high lane of
 // pack j (JV clear) and the low lane of pack j + 2^JV; scalar arithmetic.
 template <int NP, int JV>
-__device__ __forceinline__ void gate_packbit(u64 (&RE)[NP], u64 (&IM)[NP], float cm1, float s) {
+__device__ __forceinline__ void gate_packbit(u64 (&RE)[NP], u64 (&IM)[NP], float t, float s) {
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
     if (((j >> JV) & 1) == 0) {
       const int k = j | (1 << JV);
       const float2 rj = unpack2(RE[j]), ij = unpack2(IM[j]), rk = unpack2(RE[k]), ik = unpack2(IM[k]);
       float2 a = make_float2(rj.y, ij.y), b = make_float2(rk.x, ik.x);
-      rotate<float>(a, b, cm1, s);
+      shear_rotate(a, b, t, s);
       RE[j] = pack2(rj.x, a.x);
       IM[j] = pack2(ij.x, a.y);
       RE[k] = pack2(b.x, rk.y);
@@ -550,37 +682,37 @@ __device__ __forceinline__ void gate_packbit(u64 (&RE)[NP], u64 (&IM)[NP], float
 
 // combo = index of (ku < kv) among the RB(RB-1)/2 register-bit pairs in
 // lexicographic order: the first RB-1 pair the pack bit (ku = 0).
-__device__ __forceinline__ void gate_combo(u64 (&RE)[16], u64 (&IM)[16], int combo, float cm1, float s) {
+__device__ __forceinline__ void gate_combo(u64 (&RE)[16], u64 (&IM)[16], int combo, float t, float s) {
   switch (combo) {
-    case 0: gate_packbit<16, 0>(RE, IM, cm1, s); break;
-    case 1: gate_packbit<16, 1>(RE, IM, cm1, s); break;
-    case 2: gate_packbit<16, 2>(RE, IM, cm1, s); break;
-    case 3: gate_packbit<16, 3>(RE, IM, cm1, s); break;
-    case 4: gate_packed<16, 0, 1>(RE, IM, cm1, s); break;
-    case 5: gate_packed<16, 0, 2>(RE, IM, cm1, s); break;
-    case 6: gate_packed<16, 0, 3>(RE, IM, cm1, s); break;
-    case 7: gate_packed<16, 1, 2>(RE, IM, cm1, s); break;
-    case 8: gate_packed<16, 1, 3>(RE, IM, cm1, s); break;
-    default: gate_packed<16, 2, 3>(RE, IM, cm1, s); break;
+    case 0: gate_packbit<16, 0>(RE, IM, t, s); break;
+    case 1: gate_packbit<16, 1>(RE, IM, t, s); break;
+    case 2: gate_packbit<16, 2>(RE, IM, t, s); break;
+    case 3: gate_packbit<16, 3>(RE, IM, t, s); break;
+    case 4: gate_packed<16, 0, 1>(RE, IM, t, s); break;
+    case 5: gate_packed<16, 0, 2>(RE, IM, t, s); break;
+    case 6: gate_packed<16, 0, 3>(RE, IM, t, s); break;
+    case 7: gate_packed<16, 1, 2>(RE, IM, t, s); break;
+    case 8: gate_packed<16, 1, 3>(RE, IM, t, s); break;
+    default: gate_packed<16, 2, 3>(RE, IM, t, s); break;
   }
 }
-__device__ __forceinline__ void gate_combo(u64 (&RE)[32], u64 (&IM)[32], int combo, float cm1, float s) {
+__device__ __forceinline__ void gate_combo(u64 (&RE)[32], u64 (&IM)[32], int combo, float t, float s) {
   switch (combo) {
-    case 0: gate_packbit<32, 0>(RE, IM, cm1, s); break;
-    case 1: gate_packbit<32, 1>(RE, IM, cm1, s); break;
-    case 2: gate_packbit<32, 2>(RE, IM, cm1, s); break;
-    case 3: gate_packbit<32, 3>(RE, IM, cm1, s); break;
-    case 4: gate_packbit<32, 4>(RE, IM, cm1, s); break;
-    case 5: gate_packed<32, 0, 1>(RE, IM, cm1, s); break;
-    case 6: gate_packed<32, 0, 2>(RE, IM, cm1, s); break;
-    case 7: gate_packed<32, 0, 3>(RE, IM, cm1, s); break;
-    case 8: gate_packed<32, 0, 4>(RE, IM, cm1, s); break;
-    case 9: gate_packed<32, 1, 2>(RE, IM, cm1, s); break;
-    case 10: gate_packed<32, 1, 3>(RE, IM, cm1, s); break;
-    case 11: gate_packed<32, 1, 4>(RE, IM, cm1, s); break;
-    case 12: gate_packed<32, 2, 3>(RE, IM, cm1, s); break;
-    case 13: gate_packed<32, 2, 4>(RE, IM, cm1, s); break;
-    default: gate_packed<32, 3, 4>(RE, IM, cm1, s); break;
+    case 0: gate_packbit<32, 0>(RE, IM, t, s); break;
+    case 1: gate_packbit<32, 1>(RE, IM, t, s); break;
+    case 2: gate_packbit<32, 2>(RE, IM, t, s); break;
+    case 3: gate_packbit<32, 3>(RE, IM, t, s); break;
+    case 4: gate_packbit<32, 4>(RE, IM, t, s); break;
+    case 5: gate_packed<32, 0, 1>(RE, IM, t, s); break;
+    case 6: gate_packed<32, 0, 2>(RE, IM, t, s); break;
+    case 7: gate_packed<32, 0, 3>(RE, IM, t, s); break;
+    case 8: gate_packed<32, 0, 4>(RE, IM, t, s); break;
+    case 9: gate_packed<32, 1, 2>(RE, IM, t, s); break;
+    case 10: gate_packed<32, 1, 3>(RE, IM, t, s); break;
+    case 11: gate_packed<32, 1, 4>(RE, IM, t, s); break;
+    case 12: gate_packed<32, 2, 3>(RE, IM, t, s); break;
+    case 13: gate_packed<32, 2, 4>(RE, IM, t, s); break;
+    default: gate_packed<32, 3, 4>(RE, IM, t, s); break;
   }
 }
 
@@ -603,14 +735,14 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // variant, and the gate's FP32 coefficients resolved from the job's table.
 struct SOp {
   uint8_t kind, combo, arg, pad;
-  float cm1, s;
+  float t, s;  // shear coefficients of a gate
 };
 
 }  // namespace sw2
 
 // Register-blocked sweep with RB register bits (2^RB amplitudes per thread,
 // 2^(K-RB) threads per tile).
-template <int RB>
+template <int RB, bool SITES>
 __global__ void __launch_bounds__(RB == 5 ? 512 : 256)
 sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pdesc,
               const PhaseDesc *__restrict__ phases, const ROp *__restrict__ rops, int M) {
@@ -631,6 +763,7 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
   __shared__ uint32_t s_slot_amp[NA]; // their shared-memory slot (slot is XOR-linear)
   __shared__ PhaseDesc s_ph[kMaxPassPhases];
   __shared__ sw2::SOp s_op[kMaxPassOps];
+  __shared__ double s_w[SITES ? kMaxWarps * kSiteSlots : 1];
   {
     const int nwords = (int)(sizeof(PassDesc) / 4);
     for (int w = threadIdx.x; w < nwords; w += blockDim.x)
@@ -646,10 +779,10 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
     const ROp r = rops[d.rop0 + i];
     sw2::SOp o;
     o.kind = r.kind, o.combo = r.combo, o.arg = r.arg, o.pad = 0;
-    o.cm1 = 0.f, o.s = 0.f;
+    o.t = 0.f, o.s = 0.f;
     if (r.kind == OP_GATE) {
       const GateCoef g = coefs[r.coef];
-      o.cm1 = g.cm1f, o.s = g.sf;
+      o.t = g.tf, o.s = g.sft;
     }
     s_op[i] = o;
   }
@@ -801,7 +934,7 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
     for (int k = 0; k < ph.nops; ++k) {
       const sw2::SOp nxt = s_op[o0 + (k + 1 < ph.nops ? k + 1 : k)];  // prefetch
       if (cur.kind == OP_GATE) {
-        sw2::gate_combo(RE, IM, cur.combo, cur.cm1, cur.s);
+        sw2::gate_combo(RE, IM, cur.combo, cur.t, cur.s);
       } else if (cur.kind == OP_REDUCE) {
         int kr = -1;
 #pragma unroll
@@ -827,6 +960,35 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
             if (bit) up += pr.x + pr.y;
             else dn += pr.x + pr.y;
           }
+        }
+        if constexpr (SITES) {
+          // per tile bit, the weight with that bit up: register bits from the
+          // packs, thread-index bits the thread's whole sum
+          float tsum = 0.f, ureg[RB];
+#pragma unroll
+          for (int q = 0; q < RB; ++q) ureg[q] = 0.f;
+#pragma unroll
+          for (int j = 0; j < NP; ++j) {
+            const float2 pr = sw2::unpack2(sw2::fma2(RE[j], RE[j], sw2::mul2(IM[j], IM[j])));
+            const float sj = pr.x + pr.y;
+            tsum += sj;
+            ureg[0] += pr.y;
+#pragma unroll
+            for (int i = 0; i < RB - 1; ++i)
+              if ((j >> i) & 1) ureg[1 + i] += sj;
+          }
+          uint32_t tbits = 0;
+          for (int b = 0; b < 5; ++b) tbits |= ((uint32_t)(tid >> b) & 1u) << ph.lanes[b];
+          for (int b = 0; b < lognt - 5; ++b) tbits |= ((uint32_t)(tid >> (5 + b)) & 1u) << ph.warps[b];
+#pragma unroll
+          for (int q = 0; q < kMaxK; ++q) {
+            float v = ((tbits >> q) & 1u) ? tsum : 0.f;
+#pragma unroll
+            for (int k2 = 0; k2 < RB; ++k2)
+              if (ph.rb[k2] == q) v = ureg[k2];
+            warp_site_sum<float>(v, q, s_w);
+          }
+          warp_site_sum<float>(tsum, kMaxK, s_w);
         }
       }
       cur = nxt;
@@ -862,6 +1024,8 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
       *reinterpret_cast<float4 *>(dst0 + s_off_hi[e]) = make_float4(v0.x, v0.y, v1.x, v1.y);
     }
   }
+  if constexpr (SITES)
+    if (d.has_reduce) write_site_partials(d, M, base, s_w, jp.psites);
   if (d.has_reduce) reduce_finalize((double)up, (double)dn, jp, false);
 }
 

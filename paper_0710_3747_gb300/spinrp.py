@@ -76,6 +76,8 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             "spinrp_state_destroy": ([vp], None),
             "spinrp_state_init_random_phase": ([vp, ctypes.c_uint64], ctypes.c_int),
             "spinrp_state_init_product_phase": ([vp, ctypes.c_uint64], ctypes.c_int),
+            "spinrp_state_set_sites": ([vp, ctypes.c_int], ctypes.c_int),
+            "spinrp_site_series": ([vp, dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
             "spinrp_state_load": ([vp, dp], ctypes.c_int),
             "spinrp_evolve": ([vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
             "spinrp_series_length": ([vp], ctypes.c_int64),
@@ -265,6 +267,19 @@ class State:
 
     def series_length(self) -> int:
         return int(lib().spinrp_series_length(self._h))
+
+    def set_sites(self, all_sites: bool = True):
+        """All-site readout from the next init / load on."""
+        _check(lib().spinrp_state_set_sites(self._h, 1 if all_sites else 0))
+        return self
+
+    def site_series(self) -> np.ndarray:
+        """(len, M) array: P_{q1}(t_k) of every spin q."""
+        n = self.series_length()
+        out = np.empty((max(n, 1), self.M), dtype=np.float64)
+        got = ctypes.c_int64()
+        _check(lib().spinrp_site_series(self._h, _dp(out), n, ctypes.byref(got)))
+        return out[:got.value]
 
     def polarization(self, site: int = 1) -> np.ndarray:
         n = self.series_length()

@@ -223,8 +223,11 @@ def test_errors_are_reported():
         st.evolve(0.1, 1, order=4)
     assert e.value.code == spinrp.EUNSUPPORTED
     with pytest.raises(spinrp.SpinrpError) as e:
-        st.polarization(2)
-    assert e.value.code == spinrp.EUNSUPPORTED
+        st.polarization(2)  # all-site readout not enabled
+    assert e.value.code == spinrp.ESTATE
+    with pytest.raises(spinrp.SpinrpError) as e:
+        st.polarization(7)
+    assert e.value.code == spinrp.EINVAL
     with pytest.raises(spinrp.SpinrpError):
         st.evolve(float("nan"), 1)
     st.evolve(0.1, 2)
