@@ -1277,20 +1277,36 @@ std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint
   };
   const uint64_t N = 1ull << M;
   char buf[160];
-  // load: amplitude t = tid + nt*e
+  if (M - K > 31) return "more than 31 outer bits";
+  // the kernel's block origin: OR of lane contributions
+  uint64_t kbase = 0;
+  for (int lane = 0; lane < 32; ++lane)
+    if (lane < M - K) kbase |= ((block >> lane) & 1ull) << d.outer_pos[lane];
+  if (kbase != base) return "block origin";
+  auto gray = [](int g) { return g ^ (g >> 1); };
+  auto low_bit = [](int g) { int k = 0; while (!((g >> k) & 1)) ++k; return k; };
+  // load: amplitude t = tid + nt*gray(g), walked as the kernel walks it
   std::vector<char> seen(T, 0);
-  for (int tid = 0; tid < nt; ++tid)
-    for (int e = 0; e < (1 << (K - lognt)); ++e) {
-      const uint32_t t = ((uint32_t)e << lognt) | (uint32_t)tid;
-      uint64_t off = 0;
-      for (int k = 0; k < lognt; ++k) if ((tid >> k) & 1) off |= 1ull << d.tile_pos[k];
-      for (int k = 0; k < K - lognt; ++k) if ((e >> k) & 1) off |= 1ull << d.tile_pos[lognt + k];
-      const uint32_t s = host_slot(t);
-      if (t >= T || s >= T || seen[s]++ || base + off >= N || base + off != phys(t)) {
+  for (int tid = 0; tid < nt; ++tid) {
+    uint64_t off = 0;
+    for (int k = 0; k < lognt; ++k) if ((tid >> k) & 1) off |= 1ull << d.tile_pos[k];
+    int64_t elem = (int64_t)(base + off);
+    uint32_t s = host_slot((uint32_t)tid);
+    for (int g = 0; g < (1 << rb); ++g) {
+      if (g) {
+        const int k = low_bit(g);
+        const int64_t dg = (int64_t)1 << d.tile_pos[lognt + k];
+        elem += ((gray(g) >> k) & 1) ? dg : -dg;
+        s ^= host_slot(1u << (lognt + k));
+      }
+      const uint32_t t = ((uint32_t)gray(g) << lognt) | (uint32_t)tid;
+      if (t >= T || s >= T || s != host_slot(t) || seen[s]++ || elem < 0 || (uint64_t)elem >= N ||
+          (uint64_t)elem != phys(t)) {
         snprintf(buf, sizeof buf, "load index out of place (t=%u)", t);
         return buf;
       }
     }
+  }
   // phases: every thread's 32-amplitude subcube, slots by linearity of the swizzle
   for (int p = 0; p < d.nphases; ++p) {
     const PhaseDesc &ph = phases[d.phase0 + p];
@@ -1313,21 +1329,36 @@ std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint
       }
     }
   }
-  // store: output chunk 2*(tid + nt*e') of two amplitudes, 16-byte aligned
+  // store: output chunk 2*(tid + nt*gray(g)) of two amplitudes, 16-byte
+  // aligned, walked as the kernel walks it
   std::fill(seen.begin(), seen.end(), 0);
-  for (int tid = 0; tid < nt; ++tid)
-    for (int e = 0; e < (1 << (K - 1 - lognt)); ++e) {
-      const uint32_t tout = ((uint32_t)e << (lognt + 1)) | ((uint32_t)tid << 1);
+  for (int tid = 0; tid < nt; ++tid) {
+    uint64_t off_lo = 0;
+    uint32_t pin_lo = 0;
+    for (int k = 0; k < lognt; ++k)
+      if ((tid >> k) & 1) off_lo |= 1ull << d.tile_pos[1 + k], pin_lo |= 1u << d.perm[1 + k];
+    int64_t elem = (int64_t)(base + off_lo);
+    uint32_t so = host_slot(pin_lo);
+    const uint32_t sl1 = host_slot(1u << d.perm[0]);
+    for (int g = 0; g < (1 << (rb - 1)); ++g) {
+      if (g) {
+        const int k = low_bit(g);
+        const int64_t dh = (int64_t)1 << d.tile_pos[1 + lognt + k];
+        elem += ((gray(g) >> k) & 1) ? dh : -dh;
+        so ^= host_slot(1u << d.perm[1 + lognt + k]);
+      }
+      const uint32_t tout = ((uint32_t)gray(g) << (lognt + 1)) | ((uint32_t)tid << 1);
       uint32_t tin = 0;
       for (int q = 1; q < K; ++q) tin |= ((tout >> q) & 1u) << d.perm[q];
       const uint32_t tin1 = tin | (1u << d.perm[0]);
-      const uint64_t addr = phys(tout);
-      if ((addr & 1ull) || addr + 1 >= N || tin >= T || tin1 >= T || seen[host_slot(tin)]++ ||
-          seen[host_slot(tin1)]++) {
+      if (elem < 0 || (elem & 1) || (uint64_t)elem + 1 >= N || (uint64_t)elem != phys(tout) || tin >= T ||
+          tin1 >= T || so != host_slot(tin) || (so ^ sl1) != host_slot(tin1) || seen[so]++ ||
+          seen[so ^ sl1]++) {
         snprintf(buf, sizeof buf, "store index out of place (t=%u)", tout);
         return buf;
       }
     }
+  }
   return "";
 }
 }  // namespace

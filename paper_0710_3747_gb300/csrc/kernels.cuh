@@ -641,8 +641,31 @@ __device__ __forceinline__ float2 unpack2(u64 v) {
 // bits 1..RB-1.  Register bit 0 (the "pack bit") is chosen by the host as the
 // bit with the fewest gates in the phase.
 
+// In-place x += a * b on packed FP32x2 (the accumulator keeps its register,
+// so a gate leaves every pack where it found it).
+__device__ __forceinline__ void fma2_acc(u64 &x, u64 a, u64 b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(x) : "l"(a), "l"(b));
+}
+
+// Three in-place shears on the plane (high lane of P, low lane of Q) or
+// (low lane of P, high lane of Q): X += t Y, Y += n X, X += t Y.
+__device__ __forceinline__ void shear_hi_lo(u64 &P, u64 &Q, float t, float n) {
+  asm("{\n\t.reg .f32 pl, ph, ql, qh;\n\t"
+      "mov.b64 {pl, ph}, %0;\n\tmov.b64 {ql, qh}, %1;\n\t"
+      "fma.rn.f32 ph, %2, ql, ph;\n\tfma.rn.f32 ql, %3, ph, ql;\n\tfma.rn.f32 ph, %2, ql, ph;\n\t"
+      "mov.b64 %0, {pl, ph};\n\tmov.b64 %1, {ql, qh};\n\t}"
+      : "+l"(P), "+l"(Q) : "f"(t), "f"(n));
+}
+__device__ __forceinline__ void shear_lo_hi(u64 &P, u64 &Q, float t, float n) {
+  asm("{\n\t.reg .f32 pl, ph, ql, qh;\n\t"
+      "mov.b64 {pl, ph}, %0;\n\tmov.b64 {ql, qh}, %1;\n\t"
+      "fma.rn.f32 pl, %2, qh, pl;\n\tfma.rn.f32 qh, %3, pl, qh;\n\tfma.rn.f32 pl, %2, qh, pl;\n\t"
+      "mov.b64 %0, {pl, ph};\n\tmov.b64 %1, {ql, qh};\n\t}"
+      : "+l"(P), "+l"(Q) : "f"(t), "f"(n));
+}
+
 // Gate on register bits (JU + 1, JV + 1): two amplitude pairs per packed
-// instruction, same three-shear update as shear_rotate.
+// instruction, same three-shear update as shear_rotate, in place.
 template <int NP, int JU, int JV>
 __device__ __forceinline__ void gate_packed(u64 (&RE)[NP], u64 (&IM)[NP], float t, float s) {
   const u64 t2 = pack2(t, t), n2 = pack2(-s, -s);
@@ -651,12 +674,12 @@ __device__ __forceinline__ void gate_packed(u64 (&RE)[NP], u64 (&IM)[NP], float 
     if (((j >> JU) & 1) == 1 && ((j >> JV) & 1) == 0) {
       const int k = j ^ (1 << JU) ^ (1 << JV);
       // plane (Re a, Im b) = (RE[j], IM[k]); plane (Re b, Im a) = (RE[k], IM[j])
-      u64 x = fma2(t2, IM[k], RE[j]);
-      IM[k] = fma2(n2, x, IM[k]);
-      RE[j] = fma2(t2, IM[k], x);
-      x = fma2(t2, IM[j], RE[k]);
-      IM[j] = fma2(n2, x, IM[j]);
-      RE[k] = fma2(t2, IM[j], x);
+      fma2_acc(RE[j], t2, IM[k]);
+      fma2_acc(RE[k], t2, IM[j]);
+      fma2_acc(IM[k], n2, RE[j]);
+      fma2_acc(IM[j], n2, RE[k]);
+      fma2_acc(RE[j], t2, IM[k]);
+      fma2_acc(RE[k], t2, IM[j]);
     }
   }
 }
@@ -669,13 +692,10 @@ __device__ __forceinline__ void gate_packbit(u64 (&RE)[NP], u64 (&IM)[NP], float
   for (int j = 0; j < NP; ++j) {
     if (((j >> JV) & 1) == 0) {
       const int k = j | (1 << JV);
-      const float2 rj = unpack2(RE[j]), ij = unpack2(IM[j]), rk = unpack2(RE[k]), ik = unpack2(IM[k]);
-      float2 a = make_float2(rj.y, ij.y), b = make_float2(rk.x, ik.x);
-      shear_rotate(a, b, t, s);
-      RE[j] = pack2(rj.x, a.x);
-      IM[j] = pack2(ij.x, a.y);
-      RE[k] = pack2(b.x, rk.y);
-      IM[k] = pack2(b.y, ik.y);
+      // a = high lanes of pack j, b = low lanes of pack k:
+      // plane (Re a, Im b) = (RE[j].hi, IM[k].lo); plane (Re b, Im a) = (RE[k].lo, IM[j].hi)
+      shear_hi_lo(RE[j], IM[k], t, -s);
+      shear_lo_hi(RE[k], IM[j], t, -s);
     }
   }
 }
@@ -720,12 +740,15 @@ __device__ __forceinline__ void gate_combo(u64 (&RE)[32], u64 (&IM)[32], int com
 __host__ __device__ constexpr int ctz5(int g) {
   return (g & 1) ? 0 : (g & 2) ? 1 : (g & 4) ? 2 : (g & 8) ? 3 : 4;
 }
+// same for g in 1..63; gray(g) = g ^ (g >> 1) differs from gray(g - 1) in bit
+// ctz6(g), which gray(g) has set when gray_up(g)
+__host__ __device__ constexpr int ctz6(int g) { return (g & 31) ? ctz5(g & 31) : 5; }
+__host__ __device__ constexpr bool gray_up(int g) { return (((g ^ (g >> 1)) >> ctz6(g)) & 1) != 0; }
 
 // 8-byte asynchronous global->shared copy (one amplitude): the swizzle may
 // move an amplitude pair to an odd slot, so 16-byte copies would misalign.
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
-  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+__device__ __forceinline__ void cp_async8(uint32_t smem_addr, const void *gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
@@ -757,10 +780,6 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
   __shared__ uint64_t sH[kMaxK];
   __shared__ uint64_t sQ[kMaxK * kMaxK];
   __shared__ uint64_t sOut;
-  __shared__ uint64_t s_off_hi[NP];   // physical offset of the high chunk-index bits
-  __shared__ uint32_t s_slot_st[NP];  // slot of the high bits of an output chunk's input index
-  __shared__ uint64_t s_off_amp[NA];  // physical offset of the high amplitude-index bits
-  __shared__ uint32_t s_slot_amp[NA]; // their shared-memory slot (slot is XOR-linear)
   __shared__ PhaseDesc s_ph[kMaxPassPhases];
   __shared__ sw2::SOp s_op[kMaxPassOps];
   __shared__ double s_w[SITES ? kMaxWarps * kSiteSlots : 1];
@@ -772,7 +791,16 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
   __syncthreads();
   const int K = d.K, tid = threadIdx.x, nt = blockDim.x;
   const int lognt = K - RB;
-  const uint64_t base = deposit_bits(blockIdx.x, d.outer_pos, M - K);
+  // block origin: lane k places bit k of the block index at outer_pos[k]
+  // (M - K < 32 outer bits), a warp OR-reduction assembles the offset
+  uint64_t base;
+  {
+    const int lane = tid & 31;
+    const uint64_t c = lane < M - K ? (uint64_t)((blockIdx.x >> lane) & 1u) << d.outer_pos[lane] : 0ull;
+    const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)c);
+    const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(c >> 32));
+    base = ((uint64_t)hi << 32) | lo;
+  }
   // stage the pass's program: phases, and ops with their coefficients
   for (int i = tid; i < d.nphases; i += nt) s_ph[i] = phases[d.phase0 + i];
   for (int i = tid; i < d.nrops; i += nt) {
@@ -786,52 +814,42 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
     }
     s_op[i] = o;
   }
-  // output chunks of two amplitudes (tile bit 0): chunk ch = tid + nt * e
-  // covers tile index 2*ch; tile bits 1..lognt come from tid, the RB - 1 high
-  // ones from e
-  for (int e = tid; e < NP; e += nt) {
-    uint64_t o = 0;
-    uint32_t pin = 0;
-    for (int k = 0; k < RB - 1; ++k) {
-      const int q = 1 + lognt + k;
-      if ((e >> k) & 1) o |= 1ull << d.tile_pos[q], pin |= 1u << d.perm[q];
-    }
-    s_off_hi[e] = o;
-    s_slot_st[e] = sw2::slot(pin);
-  }
-  uint64_t off_lo = 0;
-  uint32_t pin_lo = 0;
-  for (int k = 0; k < lognt; ++k)
-    if ((tid >> k) & 1) off_lo |= 1ull << d.tile_pos[1 + k], pin_lo |= 1u << d.perm[1 + k];
-  // input amplitude a = tid + nt * e: tile bits 0..lognt-1 from tid, the RB
-  // high bits from e
-  for (int e = tid; e < NA; e += nt) {
-    uint64_t o = 0;
-    for (int k = 0; k < RB; ++k)
-      if ((e >> k) & 1) o |= 1ull << d.tile_pos[lognt + k];
-    s_off_amp[e] = o;
-    s_slot_amp[e] = sw2::slot((uint32_t)e << lognt);
-  }
-  uint64_t off_amp_lo = 0;
-  for (int k = 0; k < lognt; ++k)
-    if ((tid >> k) & 1) off_amp_lo |= 1ull << d.tile_pos[k];
   __syncthreads();
 
   // ---- global -> shared (8-byte async copies; 16 consecutive threads read
-  // one 128-byte run)
+  // one 128-byte run).  Input amplitude a = tid + nt * e: tile bits
+  // 0..lognt-1 from tid, the RB high bits from e, e walked in Gray-code order
+  // so that each copy moves the source by +-2^tile_pos (a compile-time sign)
+  // and the destination slot by one XOR (the slot is XOR-linear).
   {
-    const float2 *src = psi + base + off_amp_lo;
-    const uint32_t slot_lo = sw2::slot((uint32_t)tid);
+    uint64_t off_amp_lo = 0;
+    for (int k = 0; k < lognt; ++k)
+      if ((tid >> k) & 1) off_amp_lo |= 1ull << d.tile_pos[k];
+    int64_t dg[RB];
+    uint32_t ds[RB];
 #pragma unroll
-    for (int e = 0; e < NA; ++e)
-      sw2::cp_async8(&tile2[slot_lo ^ s_slot_amp[e]], src + s_off_amp[e]);
+    for (int k = 0; k < RB; ++k) {
+      dg[k] = (int64_t)8 << d.tile_pos[lognt + k];
+      ds[k] = sw2::slot(1u << (lognt + k)) << 3;
+    }
+    const char *src = reinterpret_cast<const char *>(psi + base + off_amp_lo);
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tile2);
+    uint32_t sb = sw2::slot((uint32_t)tid) << 3;
+#pragma unroll
+    for (int g = 0; g < NA; ++g) {
+      if (g) {
+        const int k = sw2::ctz6(g);
+        src += sw2::gray_up(g) ? dg[k] : -dg[k];
+        sb ^= ds[k];
+      }
+      sw2::cp_async8(sbase + sb, src);
+    }
   }
   sw2::cp_async_wait_all();
   __syncthreads();
 
   float up = 0.f, dn = 0.f;
   const int nout = M - K;
-  float *tf = reinterpret_cast<float *>(tile2);
   for (int p = 0; p < d.nphases; ++p) {
     const PhaseDesc &ph = s_ph[p];
     // slot of this thread's subcube origin (host-precomputed slot of each
@@ -917,17 +935,23 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
       continue;
     }
     // load the subcube as NP packs, walking the packs in Gray-code order so
-    // each step changes one register bit (one XOR on the slot)
+    // each step changes one register bit (one XOR on the byte offset)
     u64 RE[NP], IM[NP];
+    const char *tb = reinterpret_cast<const char *>(tile2);
+    uint32_t mb[RB];
+#pragma unroll
+    for (int k = 0; k < RB; ++k) mb[k] = sm[k] << 3;
     {
-      uint32_t s = s0;
+      uint32_t o = s0 << 3;
 #pragma unroll
       for (int g = 0; g < NP; ++g) {
-        if (g) s ^= sm[1 + sw2::ctz5(g)];
+        if (g) o ^= mb[1 + sw2::ctz5(g)];
         const int j = g ^ (g >> 1);
-        const uint32_t s1 = s ^ sm[0];
-        RE[j] = sw2::pack2(tf[2 * s], tf[2 * s1]);
-        IM[j] = sw2::pack2(tf[2 * s + 1], tf[2 * s1 + 1]);
+        const uint32_t o1 = o ^ mb[0];
+        const float2 v0 = *reinterpret_cast<const float2 *>(tb + o);
+        const float2 v1 = *reinterpret_cast<const float2 *>(tb + o1);
+        RE[j] = sw2::pack2(v0.x, v1.x);
+        IM[j] = sw2::pack2(v0.y, v1.y);
       }
     }
     sw2::SOp cur = s_op[o0];
@@ -994,34 +1018,53 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
       cur = nxt;
     }
     {
-      uint32_t s = s0;
+      char *tw = reinterpret_cast<char *>(tile2);
+      uint32_t o = s0 << 3;
 #pragma unroll
       for (int g = 0; g < NP; ++g) {
-        if (g) s ^= sm[1 + sw2::ctz5(g)];
+        if (g) o ^= mb[1 + sw2::ctz5(g)];
         const int j = g ^ (g >> 1);
-        const uint32_t s1 = s ^ sm[0];
+        const uint32_t o1 = o ^ mb[0];
         const float2 r = sw2::unpack2(RE[j]), i = sw2::unpack2(IM[j]);
-        tf[2 * s] = r.x;
-        tf[2 * s + 1] = i.x;
-        tf[2 * s1] = r.y;
-        tf[2 * s1 + 1] = i.y;
+        *reinterpret_cast<float2 *>(tw + o) = make_float2(r.x, i.x);
+        *reinterpret_cast<float2 *>(tw + o1) = make_float2(r.y, i.y);
       }
     }
     __syncthreads();
   }
 
-  // ---- shared -> global, output tile bits relabelled by perm
+  // ---- shared -> global, output tile bits relabelled by perm.  Output chunk
+  // ch = tid + nt * e of two amplitudes covers output tile index 2 ch: bits
+  // 1..lognt from tid, the RB - 1 high ones from e (Gray order again).  The
+  // amplitude there is input tile index sum of bits perm[q], so its slot is an
+  // XOR of per-bit slots; the chunk's second amplitude is output bit 0 = input
+  // bit perm[0].
   {
-    // input index of output chunk e = pin_lo | (its high bits), so its slot is
-    // slot(pin_lo) ^ s_slot_st[e]; the chunk's second amplitude is output tile
-    // bit 0 = input tile bit perm[0]
-    const uint32_t sl0 = sw2::slot(pin_lo), sl1 = sw2::slot(1u << d.perm[0]);
-    float2 *dst0 = psi + base + off_lo;
-#pragma unroll 4
-    for (int e = 0; e < NP; ++e) {
-      const uint32_t s = sl0 ^ s_slot_st[e];
-      const float2 v0 = tile2[s], v1 = tile2[s ^ sl1];
-      *reinterpret_cast<float4 *>(dst0 + s_off_hi[e]) = make_float4(v0.x, v0.y, v1.x, v1.y);
+    uint64_t off_lo = 0;
+    uint32_t pin_lo = 0;
+    for (int k = 0; k < lognt; ++k)
+      if ((tid >> k) & 1) off_lo |= 1ull << d.tile_pos[1 + k], pin_lo |= 1u << d.perm[1 + k];
+    int64_t dh[RB - 1];
+    uint32_t dsl[RB - 1];
+#pragma unroll
+    for (int k = 0; k < RB - 1; ++k) {
+      dh[k] = (int64_t)8 << d.tile_pos[1 + lognt + k];
+      dsl[k] = sw2::slot(1u << d.perm[1 + lognt + k]) << 3;
+    }
+    const char *tb = reinterpret_cast<const char *>(tile2);
+    const uint32_t sl1 = sw2::slot(1u << d.perm[0]) << 3;
+    uint32_t so = sw2::slot(pin_lo) << 3;
+    char *dst = reinterpret_cast<char *>(psi + base + off_lo);
+#pragma unroll
+    for (int g = 0; g < NP; ++g) {
+      if (g) {
+        const int k = sw2::ctz5(g);
+        dst += sw2::gray_up(g) ? dh[k] : -dh[k];
+        so ^= dsl[k];
+      }
+      const float2 v0 = *reinterpret_cast<const float2 *>(tb + so);
+      const float2 v1 = *reinterpret_cast<const float2 *>(tb + (so ^ sl1));
+      *reinterpret_cast<float4 *>(dst) = make_float4(v0.x, v0.y, v1.x, v1.y);
     }
   }
   if constexpr (SITES)

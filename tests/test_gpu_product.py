@@ -75,3 +75,28 @@ def test_fig3a_product_needs_630_realizations():
     # Trotter error at dt = 0.05 is ~1e-3, far below the statistical scales here
     assert err_prod1 > 3.0 * err_ent
     assert err_prod630 < 2.0 * err_ent
+
+
+def test_fig3b_star_one_state_of_either_kind_suffices():
+    """14-spin star with Gaussian dipolar couplings (a/b = -2): both a single
+    product state and a single entangled state stay close to the ensemble
+    (the paper's Fig. 3b); contrast with the ladder above, where the product
+    state fails by a wide margin."""
+    spinrp.lib()
+    M, dt, steps = 14, 0.02, 500
+    J = W.star_gaussian(M, 1)
+    a, bb = oracle.couplings(J, oracle.DIPOLAR)
+    times = dt * np.arange(steps + 1)
+    Pens = ed.sector_ensemble_polarization(a, bb, times)
+    rms = lambda d: float(np.sqrt(np.mean(d ** 2)))
+    n = 6
+    b = spinrp.Batch([spinrp.System(J, W.DIPOLAR) for _ in range(n)], list(range(1, n + 1)), "c64",
+                     series_cap=steps + 1)
+    b.init_product_phase().evolve(dt, steps)
+    err_prod1 = np.mean([rms(b.polarization(k) - Pens) for k in range(n)])
+    b.init_random_phase().evolve(dt, steps)
+    err_ent = np.mean([rms(b.polarization(k) - Pens) for k in range(n)])
+    b.close()
+    scale = 2.0 ** (-(M - 1) / 2)  # Chebyshev scale of one entangled state
+    assert err_ent < 2.0 * scale
+    assert err_prod1 < 3.0 * err_ent and err_prod1 < 4.0 * scale
