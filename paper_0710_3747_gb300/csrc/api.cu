@@ -214,7 +214,7 @@ struct PassSet {
 
 struct Layout {  // byte offsets inside the work buffer
   size_t series, partials, ticket, job, coefs, bvals, adiag, qdiag, passes, ops, phases, rops, stage,
-      stage_idx, psites, site_series, total;
+      stage_idx, psites, site_series, sops, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -256,6 +256,7 @@ struct spinrp_state {
   double2 *stage = nullptr;
   int64_t *stage_idx = nullptr;
   JobPtrs *d_job = nullptr;   // this state's pointer table (one job)
+  JobPtrs hjob{};             // the same, host copy (passed with each sweep launch)
   int64_t *d_step = nullptr;  // device series counter
   // CUDA graphs of kGraphSteps steady-state Trotter steps (captured on first use)
   cudaStream_t cap_stream = nullptr;
@@ -441,6 +442,7 @@ static Layout work_layout(int M, int nb, int64_t cap, const PassSet &ps, int max
   L.stage_idx = o, o = align256(o + sizeof(int64_t) * kStage);
   L.psites = o, o = align256(o + sizeof(double) * (M + 1) * (size_t)max_blocks);
   L.site_series = o, o = align256(o + sizeof(double) * M * (size_t)std::max<int64_t>(cap, 1));
+  L.sops = o, o = align256(o + sizeof(ROpRes) * std::max<size_t>(ps.rops.size(), 1));
   L.total = o;
   return L;
 }
@@ -729,6 +731,8 @@ extern "C" int spinrp_state_create(const spinrp_system *sys, int prec, void *str
   hj.a = st->d_a;
   hj.psites = st->psites;
   hj.site_series = st->site_series;
+  hj.sops = (ROpRes *)(w + st->lay.sops);
+  st->hjob = hj;
 
   auto up = [&](void *dst, const void *src, size_t n) -> cudaError_t {
     if (n == 0) return cudaSuccess;
@@ -913,6 +917,7 @@ struct LaunchCtx {
   const PhaseDesc *phases = nullptr;
   const ROp *rops = nullptr;
   const JobPtrs *jobs = nullptr;
+  JobPtrs job0{};  // host copy of the only job's pointers when njobs == 1
   int njobs = 1;
   int rb = 5;                    // register bits of the register-blocked kernel
   int sites = 0;                 // all-site readout after every reducing sweep
@@ -934,15 +939,17 @@ static int launch_pass(const LaunchCtx &c, int pass, cudaStream_t stream, bool l
   if (sizeof(R) == 4 && c.v2)
   {
     const size_t sm2 = size_t(8) << K;
-    const PassDesc *pd = c.passes + pass;
+    const PassDesc &pd = c.ps->desc[pass];
+    float2 *psi1 = c.njobs == 1 ? static_cast<float2 *>(c.job0.psi) : nullptr;
+    const ROpRes *sops1 = c.njobs == 1 ? c.job0.sops : nullptr;
     if (c.rb == 6 && c.sites)
-      sweep2_kernel<6, true><<<grid, 1 << (K - 6), sm2, stream>>>(c.jobs, pd, c.phases, c.rops, c.M);
+      sweep2_kernel<6, true><<<grid, 1 << (K - 6), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M);
     else if (c.rb == 6)
-      sweep2_kernel<6, false><<<grid, 1 << (K - 6), sm2, stream>>>(c.jobs, pd, c.phases, c.rops, c.M);
+      sweep2_kernel<6, false><<<grid, 1 << (K - 6), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M);
     else if (c.sites)
-      sweep2_kernel<5, true><<<grid, 1 << (K - 5), sm2, stream>>>(c.jobs, pd, c.phases, c.rops, c.M);
+      sweep2_kernel<5, true><<<grid, 1 << (K - 5), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M);
     else
-      sweep2_kernel<5, false><<<grid, 1 << (K - 5), sm2, stream>>>(c.jobs, pd, c.phases, c.rops, c.M);
+      sweep2_kernel<5, false><<<grid, 1 << (K - 5), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M);
   }
   else if (c.sites)
     sweep_kernel<R, true><<<grid, nt, smem, stream>>>(c.jobs, c.passes + pass, c.ops, c.M);
@@ -1097,6 +1104,7 @@ static LaunchCtx state_ctx(spinrp_state *st) {
   c.phases = st->phases;
   c.rops = st->rops;
   c.jobs = st->d_job;
+  c.job0 = st->hjob;
   c.njobs = 1;
   c.prof = st;
   return c;
@@ -1121,6 +1129,12 @@ extern "C" int spinrp_evolve(spinrp_state *st, double dt, int64_t steps, int ord
     if (st->nb > 0) {
       ++g_launches;
       coef_kernel<<<(2 * st->nb + 127) / 128, 128, 0, st->stream>>>(st->d_job, st->nb, dt);
+      CUDA_TRY(cudaGetLastError());
+    }
+    if (st->v2 && !st->ps.rops.empty()) {
+      const int nr = (int)st->ps.rops.size();
+      ++g_launches;
+      resolve_ops_kernel<<<(nr + 127) / 128, 128, 0, st->stream>>>(st->d_job, st->rops, nr);
       CUDA_TRY(cudaGetLastError());
     }
     if (st->has_diag) {
@@ -1265,8 +1279,17 @@ double check_reduce(const std::vector<cplx> &A) {
 // shared-memory slots in range and each touched exactly once per stage.
 uint32_t host_slot(uint32_t t) { return t ^ (((t >> 4) ^ (t >> 8) ^ (t >> 12)) & 15u); }
 
-std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint64_t block, int rb) {
+std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint64_t block, int rb,
+                         size_t nphases_all, size_t nrops_all) {
   const int K = d.K, nt = 1 << (K - rb), lognt = K - rb;
+  if (d.nphases < 0 || d.nphases > kMaxPassPhases || d.nrops < 0 || d.nrops > kMaxPassOps ||
+      d.phase0 < 0 || (size_t)d.phase0 + d.nphases > nphases_all || d.rop0 < 0 ||
+      (size_t)d.rop0 + d.nrops > nrops_all)
+    return "program staging out of range";
+  for (int p = 0; p < d.nphases; ++p) {
+    const int o0 = phases[d.phase0 + p].op0 - d.rop0;
+    if (o0 < 0 || o0 + phases[d.phase0 + p].nops > d.nrops) return "phase op range";
+  }
   const uint32_t T = 1u << K;
   uint64_t base = 0;
   for (int k = 0; k < M - K; ++k) base |= ((block >> k) & 1ull) << d.outer_pos[k];
@@ -1290,10 +1313,16 @@ std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint
   for (int tid = 0; tid < nt; ++tid) {
     uint64_t off = 0;
     for (int k = 0; k < lognt; ++k) if ((tid >> k) & 1) off |= 1ull << d.tile_pos[k];
-    int64_t elem = (int64_t)(base + off);
-    uint32_t s = host_slot((uint32_t)tid);
+    const int64_t elem0 = (int64_t)(base + off);
+    const uint32_t s0 = host_slot((uint32_t)tid);
+    int64_t elem = elem0;
+    uint32_t s = s0;
     for (int g = 0; g < (1 << rb); ++g) {
-      if (g) {
+      if ((g & 7) == 0) {  // a run of eight starts from the origin
+        elem = elem0, s = s0;
+        for (int k = 0; k < rb; ++k)
+          if ((gray(g) >> k) & 1) elem += (int64_t)1 << d.tile_pos[lognt + k], s ^= host_slot(1u << (lognt + k));
+      } else {
         const int k = low_bit(g);
         const int64_t dg = (int64_t)1 << d.tile_pos[lognt + k];
         elem += ((gray(g) >> k) & 1) ? dg : -dg;
@@ -1327,6 +1356,26 @@ std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint
           return buf;
         }
       }
+      // the kernel's walk over its packs: byte offsets, runs of eight
+      const uint32_t ob = s0 << 3;
+      uint32_t o = ob;
+      for (int g = 0; g < (1 << (rb - 1)); ++g) {
+        const int j = gray(g);
+        if ((g & 7) == 0) {
+          o = ob;
+          for (int k = 0; k < rb - 1; ++k)
+            if ((j >> k) & 1) o ^= (uint32_t)ph.sm[1 + k] << 3;
+        } else {
+          o ^= (uint32_t)ph.sm[1 + low_bit(g)] << 3;
+        }
+        uint32_t s = s0;
+        for (int k = 0; k < rb - 1; ++k)
+          if ((j >> k) & 1) s ^= ph.sm[1 + k];
+        if (o != (s << 3) || ((o ^ ((uint32_t)ph.sm[0] << 3)) >> 3) >= T || (o >> 3) >= T) {
+          snprintf(buf, sizeof buf, "phase %d pack walk out of place (g=%d)", p, g);
+          return buf;
+        }
+      }
     }
   }
   // store: output chunk 2*(tid + nt*gray(g)) of two amplitudes, 16-byte
@@ -1337,11 +1386,18 @@ std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint
     uint32_t pin_lo = 0;
     for (int k = 0; k < lognt; ++k)
       if ((tid >> k) & 1) off_lo |= 1ull << d.tile_pos[1 + k], pin_lo |= 1u << d.perm[1 + k];
-    int64_t elem = (int64_t)(base + off_lo);
-    uint32_t so = host_slot(pin_lo);
+    const int64_t elem0 = (int64_t)(base + off_lo);
+    const uint32_t so0 = host_slot(pin_lo);
+    int64_t elem = elem0;
+    uint32_t so = so0;
     const uint32_t sl1 = host_slot(1u << d.perm[0]);
     for (int g = 0; g < (1 << (rb - 1)); ++g) {
-      if (g) {
+      if ((g & 7) == 0) {
+        elem = elem0, so = so0;
+        for (int k = 0; k < rb - 1; ++k)
+          if ((gray(g) >> k) & 1)
+            elem += (int64_t)1 << d.tile_pos[1 + lognt + k], so ^= host_slot(1u << d.perm[1 + lognt + k]);
+      } else {
         const int k = low_bit(g);
         const int64_t dh = (int64_t)1 << d.tile_pos[1 + lognt + k];
         elem += ((gray(g) >> k) & 1) ? dh : -dh;
@@ -1384,7 +1440,8 @@ extern "C" int spinrp_system_plan_check(const spinrp_system *sys, int prec, doub
     const PassDesc &d = ps.desc[pi];
     const uint64_t nblocks = 1ull << (plan.M - K);
     for (uint64_t blk : {uint64_t(0), nblocks / 3, nblocks - 1}) {
-      const std::string e = audit_sweep2(d, ps.phases.data(), plan.M, blk, ps.rb);
+      const std::string e = audit_sweep2(d, ps.phases.data(), plan.M, blk, ps.rb, ps.phases.size(),
+                                         ps.rops.size());
       if (!e.empty()) return fail(SPINRP_EINVAL, "plan_check: pass %zu block %llu: %s", pi,
                                   (unsigned long long)blk, e.c_str());
     }
@@ -1569,6 +1626,7 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
     const size_t p_bv = per; per = align256(per + sizeof(double) * nb);
     const size_t p_a = per; per = align256(per + sizeof(double) * M * M);
     const size_t p_q = per; per = align256(per + sizeof(uint64_t) * 2 * M * M);
+    const size_t p_sops = per; per = align256(per + sizeof(ROpRes) * std::max<size_t>(g.ps.rops.size(), 1));
     const size_t total = o_job0 + per * n;
     cudaError_t e = cudaMalloc((void **)&g.dev, total);
     if (e != cudaSuccess) {
@@ -1599,6 +1657,7 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
       p.bvals = (double *)(j + p_bv);
       p.a = (double *)(j + p_a);
       p.qdiag = (uint64_t *)(j + p_q);
+      p.sops = (ROpRes *)(j + p_sops);
       hs[k] = seeds[g.jobs[k]];
       for (int q = 0; q < g.nb; ++q) bv[q] = s.b[s.bonds[q].first * M + s.bonds[q].second];
       for (int q = 0; q < M * M; ++q) am[q] = s.a[q];
@@ -1632,6 +1691,7 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
     c.phases = (const PhaseDesc *)(d + o_ph);
     c.rops = (const ROp *)(d + o_rop);
     c.jobs = g.d_jobs;
+    if (n == 1) c.job0 = hj[0];
     c.njobs = n;
   }
   // the LaunchCtx keep pointers to their group's PassSet: fix them now that
@@ -1714,6 +1774,12 @@ extern "C" int spinrp_batch_evolve(spinrp_batch *b, double dt, int64_t steps, in
       if (g.nb > 0) {
         ++g_launches;
         coef_kernel<<<dim3((2 * g.nb + 127) / 128, n), 128, 0, b->stream>>>(g.d_jobs, g.nb, dt);
+        CUDA_TRY(cudaGetLastError());
+      }
+      if (g.ps.phased && !g.ps.rops.empty()) {
+        const int nr = (int)g.ps.rops.size();
+        ++g_launches;
+        resolve_ops_kernel<<<dim3((nr + 127) / 128, n), 128, 0, b->stream>>>(g.d_jobs, g.ctx.rops, nr);
         CUDA_TRY(cudaGetLastError());
       }
       if (g.has_diag) {

@@ -89,6 +89,16 @@ struct ROp {
 
 struct GateCoef;
 
+// A phase op with its FP32 gate coefficients resolved for the current dt (one
+// array per job, rebuilt with the gate table), 16 bytes for 16-byte copies.
+struct ROpRes {
+  uint8_t kind, combo, arg, pad;
+  float t, s;  // shear coefficients tan(theta/2), sin(theta) of a gate
+  uint32_t pad2;
+};
+static_assert(sizeof(ROpRes) == 16, "ROpRes is copied in 16-byte pieces");
+static_assert(sizeof(PhaseDesc) % 4 == 0, "PhaseDesc is copied in 4-byte pieces");
+
 // Device pointers of one job (one state) as the kernels see them; a launch
 // covers gridDim.y jobs that share one sweep plan, block row y using jobs[y].
 struct JobPtrs {
@@ -105,6 +115,7 @@ struct JobPtrs {
                            // norm, column 1 + q the weight with spin q up (q logical, 0-based);
                            // nullptr when only spin 1 is read out
   double *site_series;     // all-site readout: P of spin q at entry k in site_series[k * M + q]
+  ROpRes *sops;            // register-blocked program ops with resolved coefficients
 };
 
 // Gate coefficients of exp(-i theta sigma_x) on a flip-flop pair, theta = b tau/2.

@@ -153,7 +153,7 @@ __device__ __forceinline__ void warp_site_sum(R v, int slot, double *s_w) {
 
 // After a __syncthreads that follows every warp_site_sum: block sums over the
 // warps in order, written as this block's row of the (M + 1) columns.
-__device__ void write_site_partials(const PassDesc &d, int M, uint64_t base, const double *s_w,
+__device__ void write_site_partials(const PassDesc d, int M, uint64_t base, const double *s_w,
                                     double *psites) {
   const int nw = (blockDim.x + 31) >> 5, K = d.K;
   const size_t nblk = gridDim.x, blk = blockIdx.x;
@@ -346,6 +346,24 @@ __global__ void coef_kernel(const JobPtrs *__restrict__ jobs, int nb, double dt)
   g.tf = bt;
   g.sft = bs2;
   out[k] = g;
+}
+
+// Per job: the register-blocked program's ops with their FP32 gate
+// coefficients looked up once per dt (the sweep kernels copy them as is).
+__global__ void resolve_ops_kernel(const JobPtrs *__restrict__ jobs, const ROp *__restrict__ rops,
+                                   int nrops) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrops) return;
+  const JobPtrs &jp = jobs[blockIdx.y];
+  const ROp r = rops[i];
+  ROpRes o;
+  o.kind = r.kind, o.combo = r.combo, o.arg = r.arg, o.pad = 0, o.pad2 = 0;
+  o.t = 0.f, o.s = 0.f;
+  if (r.kind == OP_GATE) {
+    const GateCoef g = jp.coefs[r.coef];
+    o.t = g.tf, o.s = g.sft;
+  }
+  jp.sops[i] = o;
 }
 
 // q[v][p][p'] (physical positions): turns of the pair phase -tau_v a_ij / 4 (the
@@ -750,16 +768,15 @@ __host__ __device__ constexpr bool gray_up(int g) { return (((g ^ (g >> 1)) >> c
 __device__ __forceinline__ void cp_async8(uint32_t smem_addr, const void *gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async4(uint32_t smem_addr, const void *gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t smem_addr, const void *gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
-
-// A phase op as staged in shared memory: kind, register-bit pair, diagonal
-// variant, and the gate's FP32 coefficients resolved from the job's table.
-struct SOp {
-  uint8_t kind, combo, arg, pad;
-  float t, s;  // shear coefficients of a gate
-};
 
 }  // namespace sw2
 
@@ -767,28 +784,24 @@ struct SOp {
 // 2^(K-RB) threads per tile).
 template <int RB, bool SITES>
 __global__ void __launch_bounds__(RB == 5 ? 512 : 256)
-sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pdesc,
-              const PhaseDesc *__restrict__ phases, const ROp *__restrict__ rops, int M) {
+sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops1,
+              const __grid_constant__ PassDesc d, const PhaseDesc *__restrict__ phases, int M) {
   using sw2::u64;
   constexpr int NA = 1 << RB, NP = NA / 2;
+  // one job (gridDim.y == 1): its amplitude and op arrays come with the launch
+  // so the tile copies can start at once; the rest of the job's pointers
+  // (and everything for a batch) from the job table
+  const bool one = gridDim.y == 1;
   const JobPtrs jp = jobs[blockIdx.y];
-  float2 *__restrict__ psi = static_cast<float2 *>(jp.psi);
-  const GateCoef *__restrict__ coefs = jp.coefs;
+  float2 *__restrict__ psi = one ? psi1 : static_cast<float2 *>(jp.psi);
   const uint64_t *__restrict__ qdiag = jp.qdiag;
   extern __shared__ __align__(16) float2 tile2[];
-  __shared__ PassDesc d;
   __shared__ uint64_t sH[kMaxK];
   __shared__ uint64_t sQ[kMaxK * kMaxK];
   __shared__ uint64_t sOut;
-  __shared__ PhaseDesc s_ph[kMaxPassPhases];
-  __shared__ sw2::SOp s_op[kMaxPassOps];
+  __shared__ __align__(16) PhaseDesc s_ph[kMaxPassPhases];
+  __shared__ __align__(16) ROpRes s_op[kMaxPassOps];
   __shared__ double s_w[SITES ? kMaxWarps * kSiteSlots : 1];
-  {
-    const int nwords = (int)(sizeof(PassDesc) / 4);
-    for (int w = threadIdx.x; w < nwords; w += blockDim.x)
-      reinterpret_cast<int *>(&d)[w] = reinterpret_cast<const int *>(pdesc)[w];
-  }
-  __syncthreads();
   const int K = d.K, tid = threadIdx.x, nt = blockDim.x;
   const int lognt = K - RB;
   // block origin: lane k places bit k of the block index at outer_pos[k]
@@ -801,26 +814,14 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
     const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(c >> 32));
     base = ((uint64_t)hi << 32) | lo;
   }
-  // stage the pass's program: phases, and ops with their coefficients
-  for (int i = tid; i < d.nphases; i += nt) s_ph[i] = phases[d.phase0 + i];
-  for (int i = tid; i < d.nrops; i += nt) {
-    const ROp r = rops[d.rop0 + i];
-    sw2::SOp o;
-    o.kind = r.kind, o.combo = r.combo, o.arg = r.arg, o.pad = 0;
-    o.t = 0.f, o.s = 0.f;
-    if (r.kind == OP_GATE) {
-      const GateCoef g = coefs[r.coef];
-      o.t = g.tf, o.s = g.sft;
-    }
-    s_op[i] = o;
-  }
-  __syncthreads();
 
   // ---- global -> shared (8-byte async copies; 16 consecutive threads read
-  // one 128-byte run).  Input amplitude a = tid + nt * e: tile bits
-  // 0..lognt-1 from tid, the RB high bits from e, e walked in Gray-code order
-  // so that each copy moves the source by +-2^tile_pos (a compile-time sign)
-  // and the destination slot by one XOR (the slot is XOR-linear).
+  // one 128-byte run), issued first.  Input amplitude a = tid + nt * e: tile
+  // bits 0..lognt-1 from tid, the RB high bits from e, e walked in Gray-code
+  // order in runs of eight: each copy moves the source by +-2^tile_pos (a
+  // compile-time sign) and the destination slot by one XOR (the slot is
+  // XOR-linear); each run starts afresh from the thread's origin, so the
+  // address chains stay short.
   {
     uint64_t off_amp_lo = 0;
     for (int k = 0; k < lognt; ++k)
@@ -832,18 +833,35 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
       dg[k] = (int64_t)8 << d.tile_pos[lognt + k];
       ds[k] = sw2::slot(1u << (lognt + k)) << 3;
     }
-    const char *src = reinterpret_cast<const char *>(psi + base + off_amp_lo);
+    const char *src0 = reinterpret_cast<const char *>(psi + base + off_amp_lo);
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tile2);
-    uint32_t sb = sw2::slot((uint32_t)tid) << 3;
+    const uint32_t sb0 = sw2::slot((uint32_t)tid) << 3;
+    const char *src = src0;
+    uint32_t sb = sb0;
 #pragma unroll
     for (int g = 0; g < NA; ++g) {
-      if (g) {
+      if ((g & 7) == 0) {
+        src = src0, sb = sb0;
+#pragma unroll
+        for (int k = 0; k < RB; ++k)
+          if (((g ^ (g >> 1)) >> k) & 1) src += dg[k], sb ^= ds[k];
+      } else {
         const int k = sw2::ctz6(g);
         src += sw2::gray_up(g) ? dg[k] : -dg[k];
         sb ^= ds[k];
       }
       sw2::cp_async8(sbase + sb, src);
     }
+  }
+  // the pass's program, with coefficients already resolved for this dt
+  {
+    const uint32_t *pw = reinterpret_cast<const uint32_t *>(phases + d.phase0);
+    const uint32_t a_ph = (uint32_t)__cvta_generic_to_shared(s_ph);
+    const int nw = d.nphases * (int)(sizeof(PhaseDesc) / 4);
+    for (int i = tid; i < nw; i += nt) sw2::cp_async4(a_ph + 4u * i, pw + i);
+    const ROpRes *so = (one ? sops1 : jp.sops) + d.rop0;
+    const uint32_t a_op = (uint32_t)__cvta_generic_to_shared(s_op);
+    for (int i = tid; i < d.nrops; i += nt) sw2::cp_async16(a_op + 16u * i, so + i);
   }
   sw2::cp_async_wait_all();
   __syncthreads();
@@ -941,12 +959,20 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
     uint32_t mb[RB];
 #pragma unroll
     for (int k = 0; k < RB; ++k) mb[k] = sm[k] << 3;
+    const uint32_t ob = s0 << 3;
     {
-      uint32_t o = s0 << 3;
+      uint32_t o = ob;
 #pragma unroll
       for (int g = 0; g < NP; ++g) {
-        if (g) o ^= mb[1 + sw2::ctz5(g)];
         const int j = g ^ (g >> 1);
+        if ((g & 7) == 0) {
+          o = ob;
+#pragma unroll
+          for (int k = 0; k < RB - 1; ++k)
+            if ((j >> k) & 1) o ^= mb[1 + k];
+        } else {
+          o ^= mb[1 + sw2::ctz5(g)];
+        }
         const uint32_t o1 = o ^ mb[0];
         const float2 v0 = *reinterpret_cast<const float2 *>(tb + o);
         const float2 v1 = *reinterpret_cast<const float2 *>(tb + o1);
@@ -954,9 +980,9 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
         IM[j] = sw2::pack2(v0.y, v1.y);
       }
     }
-    sw2::SOp cur = s_op[o0];
+    ROpRes cur = s_op[o0];
     for (int k = 0; k < ph.nops; ++k) {
-      const sw2::SOp nxt = s_op[o0 + (k + 1 < ph.nops ? k + 1 : k)];  // prefetch
+      const ROpRes nxt = s_op[o0 + (k + 1 < ph.nops ? k + 1 : k)];  // prefetch
       if (cur.kind == OP_GATE) {
         sw2::gate_combo(RE, IM, cur.combo, cur.t, cur.s);
       } else if (cur.kind == OP_REDUCE) {
@@ -1019,11 +1045,18 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
     }
     {
       char *tw = reinterpret_cast<char *>(tile2);
-      uint32_t o = s0 << 3;
+      uint32_t o = ob;
 #pragma unroll
       for (int g = 0; g < NP; ++g) {
-        if (g) o ^= mb[1 + sw2::ctz5(g)];
         const int j = g ^ (g >> 1);
+        if ((g & 7) == 0) {
+          o = ob;
+#pragma unroll
+          for (int k = 0; k < RB - 1; ++k)
+            if ((j >> k) & 1) o ^= mb[1 + k];
+        } else {
+          o ^= mb[1 + sw2::ctz5(g)];
+        }
         const uint32_t o1 = o ^ mb[0];
         const float2 r = sw2::unpack2(RE[j]), i = sw2::unpack2(IM[j]);
         *reinterpret_cast<float2 *>(tw + o) = make_float2(r.x, i.x);
@@ -1053,11 +1086,18 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pde
     }
     const char *tb = reinterpret_cast<const char *>(tile2);
     const uint32_t sl1 = sw2::slot(1u << d.perm[0]) << 3;
-    uint32_t so = sw2::slot(pin_lo) << 3;
-    char *dst = reinterpret_cast<char *>(psi + base + off_lo);
+    const uint32_t so0 = sw2::slot(pin_lo) << 3;
+    char *const dst0 = reinterpret_cast<char *>(psi + base + off_lo);
+    uint32_t so = so0;
+    char *dst = dst0;
 #pragma unroll
     for (int g = 0; g < NP; ++g) {
-      if (g) {
+      if ((g & 7) == 0) {
+        so = so0, dst = dst0;
+#pragma unroll
+        for (int k = 0; k < RB - 1; ++k)
+          if (((g ^ (g >> 1)) >> k) & 1) dst += dh[k], so ^= dsl[k];
+      } else {
         const int k = sw2::ctz5(g);
         dst += sw2::gray_up(g) ? dh[k] : -dh[k];
         so ^= dsl[k];
