@@ -257,6 +257,7 @@ struct spinrp_state {
   int64_t *stage_idx = nullptr;
   JobPtrs *d_job = nullptr;   // this state's pointer table (one job)
   JobPtrs hjob{};             // the same, host copy (passed with each sweep launch)
+  unsigned prefetch_ahead = 0;  // L2 prefetch distance of the register-blocked sweep
   int64_t *d_step = nullptr;  // device series counter
   // CUDA graphs of kGraphSteps steady-state Trotter steps (captured on first use)
   cudaStream_t cap_stream = nullptr;
@@ -645,6 +646,26 @@ static int set_smem_limits() {
   return SPINRP_OK;
 }
 
+// Register-blocked sweep blocks resident on the whole device at once (the L2
+// prefetch distance); 0 when the query fails.
+static unsigned sweep2_resident(int rb, int K) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const size_t smem = size_t(8) << K;
+  const cudaError_t e =
+      rb == 6 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep2_kernel<6, false>, 1 << (K - 6), smem)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep2_kernel<5, false>, 1 << (K - 5), smem);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (unsigned)(per * sms);
+}
+
 extern "C" int spinrp_state_create(const spinrp_system *sys, int prec, void *stream,
                                    int64_t series_cap, void *psi, void *work, spinrp_state **out) {
   if (!out) return fail(SPINRP_EINVAL, "state_create: out is NULL");
@@ -756,6 +777,7 @@ extern "C" int spinrp_state_create(const spinrp_system *sys, int prec, void *str
     free_state(st);
     return rc;
   }
+  if (st->ps.phased) st->prefetch_ahead = sweep2_resident(st->ps.rb, st->plan.K);
   *out = st;
   return SPINRP_OK;
 }
@@ -921,6 +943,7 @@ struct LaunchCtx {
   int njobs = 1;
   int rb = 5;                    // register bits of the register-blocked kernel
   int sites = 0;                 // all-site readout after every reducing sweep
+  unsigned prefetch_ahead = 0;   // sweep blocks resident at once (L2 prefetch distance), 0 = off
   spinrp_state *prof = nullptr;  // state whose profiling marks to record, if any
 };
 
@@ -941,15 +964,20 @@ static int launch_pass(const LaunchCtx &c, int pass, cudaStream_t stream, bool l
     const size_t sm2 = size_t(8) << K;
     const PassDesc &pd = c.ps->desc[pass];
     float2 *psi1 = c.njobs == 1 ? static_cast<float2 *>(c.job0.psi) : nullptr;
+    const unsigned ahead = c.prefetch_ahead;
     const ROpRes *sops1 = c.njobs == 1 ? c.job0.sops : nullptr;
     if (c.rb == 6 && c.sites)
-      sweep2_kernel<6, true><<<grid, 1 << (K - 6), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M);
+      sweep2_kernel<6, true><<<grid, 1 << (K - 6), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M,
+                                                                        ahead);
     else if (c.rb == 6)
-      sweep2_kernel<6, false><<<grid, 1 << (K - 6), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M);
+      sweep2_kernel<6, false><<<grid, 1 << (K - 6), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M,
+                                                                        ahead);
     else if (c.sites)
-      sweep2_kernel<5, true><<<grid, 1 << (K - 5), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M);
+      sweep2_kernel<5, true><<<grid, 1 << (K - 5), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M,
+                                                                        ahead);
     else
-      sweep2_kernel<5, false><<<grid, 1 << (K - 5), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M);
+      sweep2_kernel<5, false><<<grid, 1 << (K - 5), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M,
+                                                                        ahead);
   }
   else if (c.sites)
     sweep_kernel<R, true><<<grid, nt, smem, stream>>>(c.jobs, c.passes + pass, c.ops, c.M);
@@ -1096,6 +1124,7 @@ static LaunchCtx state_ctx(spinrp_state *st) {
   c.v2 = st->v2;
   c.rb = st->ps.rb;
   c.sites = st->sites ? 1 : 0;
+  c.prefetch_ahead = st->prefetch_ahead;
   c.segments = st->plan.segments();
   c.sweeps_per_step = st->plan.sweeps_per_step();
   c.ps = &st->ps;
@@ -1693,6 +1722,7 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
     c.jobs = g.d_jobs;
     if (n == 1) c.job0 = hj[0];
     c.njobs = n;
+
   }
   // the LaunchCtx keep pointers to their group's PassSet: fix them now that
   // the group vector no longer moves
@@ -1716,6 +1746,8 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
     free_batch(b);
     return rc;
   }
+  for (BatchGroup &g : b->groups)
+    if (g.ps.phased) g.ctx.prefetch_ahead = sweep2_resident(g.ps.rb, g.plan.K);
   *out = b;
   return SPINRP_OK;
 }

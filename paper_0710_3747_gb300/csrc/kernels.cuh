@@ -785,7 +785,8 @@ __device__ __forceinline__ void cp_async_wait_all() {
 template <int RB, bool SITES>
 __global__ void __launch_bounds__(RB == 5 ? 512 : 256)
 sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops1,
-              const __grid_constant__ PassDesc d, const PhaseDesc *__restrict__ phases, int M) {
+              const __grid_constant__ PassDesc d, const PhaseDesc *__restrict__ phases, int M,
+              unsigned ahead) {
   using sw2::u64;
   constexpr int NA = 1 << RB, NP = NA / 2;
   // one job (gridDim.y == 1): its amplitude and op arrays come with the launch
@@ -862,6 +863,23 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops
     const ROpRes *so = (one ? sops1 : jp.sops) + d.rop0;
     const uint32_t a_op = (uint32_t)__cvta_generic_to_shared(s_op);
     for (int i = tid; i < d.nrops; i += nt) sw2::cp_async16(a_op + 16u * i, so + i);
+  }
+  // L2 prefetch of the tile of block blockIdx.x + ahead (ahead = blocks
+  // resident at once): DRAM keeps streaming while tiles compute, and that
+  // block's copies find its tile in L2.  One 128-byte run (tile bits 0..3,
+  // the low physical bits) per request.
+  if (ahead && blockIdx.x + ahead < gridDim.x) {
+    const unsigned pb = blockIdx.x + ahead;
+    const int lane = tid & 31;
+    const uint64_t c = lane < M - K ? (uint64_t)((pb >> lane) & 1u) << d.outer_pos[lane] : 0ull;
+    const uint64_t base2 = ((uint64_t)__reduce_or_sync(0xffffffffu, (uint32_t)(c >> 32)) << 32) |
+                           __reduce_or_sync(0xffffffffu, (uint32_t)c);
+    for (int r = tid; r < (1 << (K - 4)); r += nt) {
+      uint64_t off = base2;
+      for (int q = 4; q < K; ++q)
+        if ((r >> (q - 4)) & 1) off |= 1ull << d.tile_pos[q];
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(psi + off));
+    }
   }
   sw2::cp_async_wait_all();
   __syncthreads();
