@@ -460,6 +460,8 @@ static int default_regbits(int K) { return K >= 11 ? 6 : 5; }
 // phases by the same greedy as the sweep planner (gates on disjoint bits may
 // be exchanged, nothing else), and each element-wise op runs in the phase
 // after the gates it follows.
+constexpr int kPhaseBeam = 8;  // beam width of the phase planner
+
 static bool compile_phases(PassSet *ps, int K, int RB, std::string *err) {
   ps->phases.clear();
   ps->rops.clear();
@@ -504,26 +506,41 @@ static bool compile_phases(PassSet *ps, int K, int RB, std::string *err) {
       ps->phases.back().nops++;
     };
     bool last_is_diag = false;  // the last phase is a diagonal-only phase
+    // an element-wise op (the readout) between gates of one group: gates
+    // before it must all be applied first; it runs inside the phase that
+    // completes them (each thread reads its own amplitudes, whose gates so far
+    // acted within the thread's subcube)
+    int fence = -1;
+    ROp fence_op{};
     auto flush = [&](std::vector<const Op *> &gates) {
       if (gates.empty()) return true;
       last_is_diag = false;
       std::vector<std::pair<int, int>> pairs;
       for (const Op *g : gates) pairs.push_back({g->u, g->v});
-      Plan pp;
-      if (!build_plan(K, pairs, RB, 0, &pp, err)) return false;
-      for (int k = 0; k < pp.segments(); ++k) {
+      std::vector<uint32_t> sets;
+      std::vector<std::vector<int>> applied;
+      const int fz = fence < 0 ? (int)gates.size() : fence;
+      int pre_done = 0;
+      if (!plan_phases(K, pairs, RB, kPhaseBeam, fz, &sets, &applied)) {
+        *err = "phase planning failed";
+        return false;
+      }
+      for (size_t k = 0; k < sets.size(); ++k) {
+        std::vector<int> rb;
+        for (int q = 0; q < K; ++q)
+          if ((sets[k] >> q) & 1) rb.push_back(q);
         // register bit 0 is the pack bit of the complex64 kernel: the bit the
         // fewest of this phase's gates touch (their arithmetic is scalar)
-        std::vector<int> rb = pp.segQ[k];
         int pack = 0, best = 1 << 30;
         for (int q = 0; q < (int)rb.size(); ++q) {
           int n = 0;
-          for (const PlanGate &g : pp.seg[k]) n += (g.i == rb[q]) + (g.j == rb[q]);
+          for (int gi : applied[k]) n += (pairs[gi].first == rb[q]) + (pairs[gi].second == rb[q]);
           if (n < best) best = n, pack = q;
         }
         std::rotate(rb.begin(), rb.begin() + pack, rb.begin() + pack + 1);
         new_phase(rb);
-        for (const PlanGate &g : pp.seg[k]) {
+        for (int gi : applied[k]) {
+          const PlanGate g{gi, pairs[gi].first, pairs[gi].second};
           int ku = (int)(std::find(rb.begin(), rb.end(), g.i) - rb.begin());
           int kv = (int)(std::find(rb.begin(), rb.end(), g.j) - rb.begin());
           if (ku > kv) std::swap(ku, kv);
@@ -535,8 +552,10 @@ static bool compile_phases(PassSet *ps, int K, int RB, std::string *err) {
           r.combo = (uint8_t)(base_idx + (kv - ku - 1));
           r.coef = gates[g.bond]->coef;
           push_rop(r);
+          if (fence >= 0 && gi < fence && ++pre_done == fence) push_rop(fence_op);
         }
       }
+      fence = -1;
       gates.clear();
       return true;
     };
@@ -547,10 +566,15 @@ static bool compile_phases(PassSet *ps, int K, int RB, std::string *err) {
         gates.push_back(&op);
         continue;
       }
-      if (!flush(gates)) return false;
       ROp r{};
       r.kind = op.kind;
       r.arg = op.arg;
+      if (op.kind == OP_REDUCE && !gates.empty() && fence < 0) {
+        fence = (int)gates.size();
+        fence_op = r;
+        continue;
+      }
+      if (!flush(gates)) return false;
       if (op.kind == OP_DIAG) {
         // the diagonal phase runs alone (its own phase, no register subcube)
         if (!pending.empty()) new_phase(default_rb);

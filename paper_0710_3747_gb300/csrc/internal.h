@@ -154,4 +154,13 @@ int report_error(int code, const char *msg);
 bool build_plan(int M, const std::vector<std::pair<int, int>> &bonds, int K, int c, Plan *plan,
                 std::string *err);
 
+// Phases of a pass for the register-blocked kernel: gates (pairs of tile bits,
+// in order) cut into register sets of RB of the K tile bits; sets[k] (bit
+// mask) applies the gates applied[k], in an order that keeps every bit's gate
+// sequence, and no gate from index `fence` on before every gate ahead of it
+// (an element-wise op sits between them).  Beam search of width `beam` for
+// few phases.  False if a gate cannot be placed.
+bool plan_phases(int K, const std::vector<std::pair<int, int>> &gates, int RB, int beam, int fence,
+                 std::vector<uint32_t> *sets, std::vector<std::vector<int>> *applied);
+
 }  // namespace spinrp

@@ -224,4 +224,142 @@ bool build_plan(int M, const std::vector<std::pair<int, int>> &bonds, int K, int
   return true;
 }
 
+
+// ---------------------------------------------------------------------------
+// Phases of the register-blocked sweep: the gates of a pass (on its K tile
+// bits) are applied in phases, each holding RB tile bits in registers.  A
+// phase applies every gate both of whose bits it holds as soon as all earlier
+// gates on those bits are done (so each bit keeps its gate sequence and the
+// operator is unchanged).  Fewer phases mean fewer shared-memory round trips;
+// a beam search over the register sets looks further ahead than the greedy
+// segment planner.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct PhaseState {
+  std::vector<uint8_t> ptr;  // per bit: gates of its chain done
+  int done = 0;
+  int pre = 0;               // gates before the fence done
+  int parent = -1;           // index into the previous beam level
+  uint32_t set = 0;          // register set that produced this state
+};
+
+// Apply every gate reachable inside bit set R (smallest index first); gates
+// from `fence` on only once every gate before it is done (*pre counts those).
+int phase_closure(const std::vector<std::pair<int, int>> &g, const std::vector<std::vector<int>> &chain,
+                  std::vector<uint8_t> &ptr, uint32_t R, int fence, int *pre, std::vector<int> *out) {
+  auto ready = [&](int b) {
+    const int u = g[b].first, v = g[b].second;
+    return (b < fence || *pre == fence) && ptr[u] < chain[u].size() && chain[u][ptr[u]] == b &&
+           ptr[v] < chain[v].size() && chain[v][ptr[v]] == b;
+  };
+  int applied = 0;
+  for (bool progress = true; progress;) {
+    progress = false;
+    int best = -1;
+    for (int q = 0; q < (int)chain.size(); ++q) {
+      if (!((R >> q) & 1) || ptr[q] >= chain[q].size()) continue;
+      const int b = chain[q][ptr[q]];
+      if (((R >> g[b].first) & 1) && ((R >> g[b].second) & 1) && ready(b) && (best < 0 || b < best)) best = b;
+    }
+    if (best >= 0) {
+      ++ptr[g[best].first];
+      ++ptr[g[best].second];
+      ++applied;
+      if (best < fence) ++*pre;
+      if (out) out->push_back(best);
+      progress = true;
+    }
+  }
+  return applied;
+}
+
+}  // namespace
+
+bool plan_phases(int K, const std::vector<std::pair<int, int>> &gates, int RB, int beam, int fence,
+                 std::vector<uint32_t> *sets, std::vector<std::vector<int>> *applied) {
+  sets->clear();
+  applied->clear();
+  const int n = (int)gates.size();
+  if (n == 0) return true;
+  std::vector<std::vector<int>> chain(K);
+  for (int b = 0; b < n; ++b) {
+    if (gates[b].first < 0 || gates[b].first >= K || gates[b].second < 0 || gates[b].second >= K ||
+        gates[b].first == gates[b].second)
+      return false;
+    chain[gates[b].first].push_back(b);
+    chain[gates[b].second].push_back(b);
+  }
+  std::vector<std::vector<PhaseState>> levels(1);
+  if (fence < 0 || fence > n) fence = n;
+  levels[0].push_back(PhaseState{std::vector<uint8_t>(K, 0), 0, 0, -1, 0});
+  for (int depth = 0; depth < 4 * n + 4; ++depth) {
+    const std::vector<PhaseState> &cur = levels.back();
+    std::vector<PhaseState> next;
+    for (int si = 0; si < (int)cur.size(); ++si) {
+      const PhaseState &st = cur[si];
+      // bits with gates still to do; a useful set holds RB of them (all of
+      // them when fewer remain), padded with idle bits
+      std::vector<int> live;
+      for (int q = 0; q < K; ++q)
+        if (st.ptr[q] < chain[q].size()) live.push_back(q);
+      const int take = std::min<int>(RB, (int)live.size());
+      std::vector<int> pick(take);
+      for (int i = 0; i < take; ++i) pick[i] = i;
+      while (true) {
+        uint32_t R = 0;
+        for (int i : pick) R |= 1u << live[i];
+        for (int q = 0; q < K && __builtin_popcount(R) < RB; ++q) R |= 1u << q;
+        PhaseState ch{st.ptr, st.done, st.pre, si, R};
+        const int a = phase_closure(gates, chain, ch.ptr, R, fence, &ch.pre, nullptr);
+        if (a > 0) {
+          ch.done += a;
+          next.push_back(std::move(ch));
+        }
+        // next combination of `take` out of live.size()
+        int i = take - 1;
+        while (i >= 0 && pick[i] == (int)live.size() - take + i) --i;
+        if (i < 0) break;
+        ++pick[i];
+        for (int j = i + 1; j < take; ++j) pick[j] = pick[j - 1] + 1;
+      }
+    }
+    if (next.empty()) return false;
+    // keep the `beam` best distinct states (most gates done)
+    std::stable_sort(next.begin(), next.end(),
+                     [](const PhaseState &a, const PhaseState &b) { return a.done > b.done; });
+    std::vector<PhaseState> kept;
+    for (PhaseState &c : next) {
+      bool dup = false;
+      for (const PhaseState &k : kept)
+        if (k.ptr == c.ptr) {
+          dup = true;
+          break;
+        }
+      if (!dup) kept.push_back(std::move(c));
+      if ((int)kept.size() >= beam) break;
+    }
+    levels.push_back(std::move(kept));
+    if (levels.back().front().done == n) {
+      // walk back the sets of the first finished state, then replay them
+      std::vector<uint32_t> path;
+      for (int lv = (int)levels.size() - 1, si = 0; lv > 0; --lv) {
+        path.push_back(levels[lv][si].set);
+        si = levels[lv][si].parent;
+      }
+      std::reverse(path.begin(), path.end());
+      std::vector<uint8_t> ptr(K, 0);
+      int pre = 0;
+      for (uint32_t R : path) {
+        std::vector<int> out;
+        phase_closure(gates, chain, ptr, R, fence, &pre, &out);
+        sets->push_back(R);
+        applied->push_back(out);
+      }
+      return true;
+    }
+  }
+  return false;
+}
+
 }  // namespace spinrp
