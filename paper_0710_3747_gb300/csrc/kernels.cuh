@@ -874,10 +874,17 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops
     const uint64_t c = lane < M - K ? (uint64_t)((pb >> lane) & 1u) << d.outer_pos[lane] : 0ull;
     const uint64_t base2 = ((uint64_t)__reduce_or_sync(0xffffffffu, (uint32_t)(c >> 32)) << 32) |
                            __reduce_or_sync(0xffffffffu, (uint32_t)c);
-    for (int r = tid; r < (1 << (K - 4)); r += nt) {
-      uint64_t off = base2;
-      for (int q = 4; q < K; ++q)
-        if ((r >> (q - 4)) & 1) off |= 1ull << d.tile_pos[q];
+    // run r = tid + nt * i (tile bits 4.. of its first amplitude): bits from
+    // tid once, then the RB - 4 high bits per run
+    uint64_t ot = base2;
+    for (int b = 0; b < lognt; ++b)
+      if ((tid >> b) & 1) ot |= 1ull << d.tile_pos[4 + b];
+#pragma unroll
+    for (int i = 0; i < (1 << (RB - 4)); ++i) {
+      uint64_t off = ot;
+#pragma unroll
+      for (int b = 0; b < RB - 4; ++b)
+        if ((i >> b) & 1) off |= 1ull << d.tile_pos[4 + lognt + b];
       asm volatile("prefetch.global.L2 [%0];" ::"l"(psi + off));
     }
   }
@@ -951,19 +958,41 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops
         }
         G[k] = g;
       }
-      for (int i = 0; i < NA; ++i) {
-        uint32_t s = s0;
-        uint64_t th = th0;
+      // the register combinations in Gray-code order: with sigma_k = +1 for a
+      // set bit and -1 for a clear one, Theta = th0 + sum_k sigma_k G_k +
+      // sum_{k<l} sigma_k sigma_l Q_kl; flipping bit k changes Theta by
+      // -2 sigma_k F_k, F_k = G_k + sum_{l!=k} sigma_l Q_kl its field, and
+      // every other field F_l by -2 sigma_k Q_kl (exact, modulo 2^64)
+      uint64_t Qr[RB][RB], F[RB];
 #pragma unroll
-        for (int k = 0; k < RB; ++k) {
-          const uint32_t bk = (i >> k) & 1;
-          if (bk) s ^= sm[k];
-          th += bk ? G[k] : (0ull - G[k]);
+      for (int k = 0; k < RB; ++k)
 #pragma unroll
-          for (int l = k + 1; l < RB; ++l) {
-            const uint64_t v = sQ[ph.rb[k] * K + ph.rb[l]];
-            th += (bk ^ ((i >> l) & 1)) ? (0ull - v) : v;
-          }
+        for (int l = 0; l < RB; ++l)
+          Qr[k][l] = k == l ? 0ull : sQ[ph.rb[k < l ? k : l] * K + ph.rb[k < l ? l : k]];
+      uint64_t th = th0;
+#pragma unroll
+      for (int k = 0; k < RB; ++k) {
+        th -= G[k];
+        F[k] = G[k];
+#pragma unroll
+        for (int l = 0; l < RB; ++l) {
+          if (l == k) continue;
+          F[k] -= Qr[k][l];
+          if (l > k) th += Qr[k][l];
+        }
+      }
+      uint32_t s = s0;
+#pragma unroll
+      for (int g = 0; g < NA; ++g) {
+        if (g) {
+          const int k = sw2::ctz6(g);
+          // sigma_k before the flip: +1 when the bit is set in gray(g - 1)
+          const bool was_up = ((((g - 1) ^ ((g - 1) >> 1)) >> k) & 1) != 0;
+          th += was_up ? (0ull - 2ull * F[k]) : 2ull * F[k];
+#pragma unroll
+          for (int l = 0; l < RB; ++l)
+            if (l != k) F[l] += was_up ? (0ull - 2ull * Qr[l][k]) : 2ull * Qr[l][k];
+          s ^= sm[k];
         }
         tile2[s] = cmul(tile2[s], cis_turns(th, 0.0f));
       }
