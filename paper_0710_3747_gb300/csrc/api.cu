@@ -327,6 +327,7 @@ static void build_passes(const Plan &p, bool has_diag, PassSet *ps) {
     d.site_tile = -1;
     for (int q = 0; q < K; ++q)
       if (tpos[q] == Lin[0]) d.site_tile = q;
+    for (int i = 0; i + 1 < K; ++i) d.store_bit[i] = (uint8_t)(i + 1);
     d.op0 = (int)ps->ops.size();
     d.nops = 0;
     ps->desc.push_back(d);
@@ -466,6 +467,32 @@ static bool compile_phases(PassSet *ps, int K, int RB, std::string *err) {
   ps->phases.clear();
   ps->rops.clear();
   for (PassDesc &d : ps->desc) {
+    // store order: chunk-index bits 0..2 are output bits 1..3 (128-byte runs);
+    // the fourth, the last lane bit of a half-warp, is the output bit whose
+    // input bit completes four distinct slot residues, so the half-warp's
+    // 8-byte gathers from the tile hit 16 distinct bank pairs
+    {
+      auto nib = [&](int q) { return swizzle_slot(1u << d.perm[q]) & 15u; };
+      std::vector<int> order = {1, 2, 3};
+      int pick = -1;
+      for (int x = 4; x < K && pick < 0; ++x) {
+        const uint32_t a = nib(1), b = nib(2), c = nib(3), e = nib(x);
+        // independence of the four nibbles over GF(2)
+        bool indep = true;
+        for (int m = 1; m < 16 && indep; ++m) {
+          const uint32_t v = ((m & 1) ? a : 0u) ^ ((m & 2) ? b : 0u) ^ ((m & 4) ? c : 0u) ^ ((m & 8) ? e : 0u);
+          if (v == 0u) indep = false;
+        }
+        if (indep) pick = x;
+      }
+      if (K >= 5) {
+        if (pick < 0) pick = 4;
+        order.push_back(pick);
+        for (int x = 4; x < K; ++x)
+          if (x != pick) order.push_back(x);
+        for (int i = 0; i + 1 < K; ++i) d.store_bit[i] = (uint8_t)order[i];
+      }
+    }
     d.phase0 = (int)ps->phases.size();
     d.nphases = 0;
     d.rop0 = (int)ps->rops.size();
@@ -1438,7 +1465,7 @@ std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint
     uint64_t off_lo = 0;
     uint32_t pin_lo = 0;
     for (int k = 0; k < lognt; ++k)
-      if ((tid >> k) & 1) off_lo |= 1ull << d.tile_pos[1 + k], pin_lo |= 1u << d.perm[1 + k];
+      if ((tid >> k) & 1) off_lo |= 1ull << d.tile_pos[d.store_bit[k]], pin_lo |= 1u << d.perm[d.store_bit[k]];
     const int64_t elem0 = (int64_t)(base + off_lo);
     const uint32_t so0 = host_slot(pin_lo);
     int64_t elem = elem0;
@@ -1449,14 +1476,20 @@ std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint
         elem = elem0, so = so0;
         for (int k = 0; k < rb - 1; ++k)
           if ((gray(g) >> k) & 1)
-            elem += (int64_t)1 << d.tile_pos[1 + lognt + k], so ^= host_slot(1u << d.perm[1 + lognt + k]);
+            elem += (int64_t)1 << d.tile_pos[d.store_bit[lognt + k]],
+                so ^= host_slot(1u << d.perm[d.store_bit[lognt + k]]);
       } else {
         const int k = low_bit(g);
-        const int64_t dh = (int64_t)1 << d.tile_pos[1 + lognt + k];
+        const int64_t dh = (int64_t)1 << d.tile_pos[d.store_bit[lognt + k]];
         elem += ((gray(g) >> k) & 1) ? dh : -dh;
-        so ^= host_slot(1u << d.perm[1 + lognt + k]);
+        so ^= host_slot(1u << d.perm[d.store_bit[lognt + k]]);
       }
-      const uint32_t tout = ((uint32_t)gray(g) << (lognt + 1)) | ((uint32_t)tid << 1);
+      // output tile index of chunk c = tid + nt * gray(g): chunk-index bit i is
+      // output bit store_bit[i]; the chunk's first amplitude has output bit 0 clear
+      const uint32_t c = ((uint32_t)gray(g) << lognt) | (uint32_t)tid;
+      uint32_t tout = 0;
+      for (int i = 0; i + 1 < K; ++i)
+        if ((c >> i) & 1) tout |= 1u << d.store_bit[i];
       uint32_t tin = 0;
       for (int q = 1; q < K; ++q) tin |= ((tout >> q) & 1u) << d.perm[q];
       const uint32_t tin1 = tin | (1u << d.perm[0]);

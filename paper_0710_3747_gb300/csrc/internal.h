@@ -47,6 +47,7 @@ struct PassDesc {
   int32_t nphases;      //   and number of phases,
   int32_t rop0;         //   first op
   int32_t nrops;        //   and number of ops
+  uint8_t store_bit[kMaxK];  // store: output tile bit (1..K-1) of each chunk-index bit
 };
 
 // Register-blocked execution of a pass (complex64 path).  In a phase every

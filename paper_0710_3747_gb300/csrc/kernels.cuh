@@ -1123,13 +1123,17 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops
     uint64_t off_lo = 0;
     uint32_t pin_lo = 0;
     for (int k = 0; k < lognt; ++k)
-      if ((tid >> k) & 1) off_lo |= 1ull << d.tile_pos[1 + k], pin_lo |= 1u << d.perm[1 + k];
+      if ((tid >> k) & 1) {
+        const int q = d.store_bit[k];
+        off_lo |= 1ull << d.tile_pos[q], pin_lo |= 1u << d.perm[q];
+      }
     int64_t dh[RB - 1];
     uint32_t dsl[RB - 1];
 #pragma unroll
     for (int k = 0; k < RB - 1; ++k) {
-      dh[k] = (int64_t)8 << d.tile_pos[1 + lognt + k];
-      dsl[k] = sw2::slot(1u << d.perm[1 + lognt + k]) << 3;
+      const int q = d.store_bit[lognt + k];
+      dh[k] = (int64_t)8 << d.tile_pos[q];
+      dsl[k] = sw2::slot(1u << d.perm[q]) << 3;
     }
     const char *tb = reinterpret_cast<const char *>(tile2);
     const uint32_t sl1 = sw2::slot(1u << d.perm[0]) << 3;
