@@ -119,13 +119,12 @@ struct JobPtrs {
   ROpRes *sops;            // register-blocked program ops with resolved coefficients
 };
 
-// Gate coefficients of exp(-i theta sigma_x) on a flip-flop pair, theta = b tau/2.
-// FP64: (cos theta - 1, sin theta), so that small rotations keep their
-// relative precision: x' = x + cm1 x - i s y.  FP32: (tan theta/2, sin theta)
-// of the three-shear form of the two real plane rotations the gate is made of
-// (see shear_rotate).
+// Gate coefficients of exp(-i theta sigma_x) on a flip-flop pair, theta = b tau/2:
+// (tan theta/2, sin theta) of the three-shear form of the two real plane
+// rotations the gate is made of (see shear_rotate), in FP64 and as the FP32
+// pair closest to a rotation.
 struct GateCoef {
-  double cm1, s;
+  double t, s;
   float tf, sft;
 };
 

@@ -325,15 +325,13 @@ __global__ void coef_kernel(const JobPtrs *__restrict__ jobs, int nb, double dt)
   GateCoef *__restrict__ out = const_cast<GateCoef *>(jobs[blockIdx.y].coefs);
   const double tau = (k & 1) ? dt : 0.5 * dt;
   const double th = 0.5 * bvals[k >> 1] * tau;  // exp(-i tau b (SxSx+SySy)) = cos th - i sin th sigma_x
-  const double s = sin(th), h = sin(0.5 * th);
-  const double cm1 = -2.0 * h * h;  // cos th - 1 without cancellation
+  const double s = sin(th);
   GateCoef g;
-  g.cm1 = cm1;
   g.s = s;
+  g.t = tan(0.5 * th);
   // FP32 shear pair: among +-2 ulps of the rounded values, the one closest to a
   // rotation, |s (1 + t^2) - 2 t| (zero exactly when s = sin 2 atan t)
-  const double tt = tan(0.5 * th);
-  const float t0 = (float)tt, s1 = (float)s;
+  const float t0 = (float)g.t, s1 = (float)s;
   float bt = t0, bs2 = s1;
   double best2 = fabs((double)s1 * (1.0 + (double)t0 * t0) - 2.0 * (double)t0);
   for (int dtt = -2; dtt <= 2; ++dtt)
@@ -391,7 +389,7 @@ __global__ void diag_kernel(const JobPtrs *__restrict__ jobs, LayoutArg lay, int
 // One sweep.  Each block owns one tile: it loads the tile's 2^K amplitudes
 // into shared memory, applies the pass's ops in order and stores the tile.
 // ---------------------------------------------------------------------------
-// FP32 gate as two real plane rotations: exp(-i theta sigma_x) maps
+// A gate as two real plane rotations: exp(-i theta sigma_x) maps
 // (Re a, Im b) and (Re b, Im a) each by [[c, s], [-s, c]], c = cos theta,
 // s = sin theta, and each rotation is three shears x += t y, y -= s x,
 // x += t y with t = tan(theta/2): three FMAs per plane.  A shear has
@@ -405,18 +403,15 @@ __device__ __forceinline__ void shear_rotate(float2 &a, float2 &b, float t, floa
   a.y = fmaf(-s, x, a.y);
   b.x = fmaf(t, a.y, x);
 }
-
-// FP64 gate: a' = a + cm1 a - i s b ; b' = b + cm1 b - i s a (cm1 = cos - 1).
-template <typename R>
-__device__ __forceinline__ void rotate(typename CT<R>::T &a, typename CT<R>::T &b, R cm1, R s);
-template <>
-__device__ __forceinline__ void rotate<double>(double2 &a, double2 &b, double cm1, double s) {
-  const double ax = a.x, ay = a.y, bx = b.x, by = b.y;
-  a.x = fma(s, by, fma(cm1, ax, ax));
-  a.y = fma(-s, bx, fma(cm1, ay, ay));
-  b.x = fma(s, ay, fma(cm1, bx, bx));
-  b.y = fma(-s, ax, fma(cm1, by, by));
+__device__ __forceinline__ void shear_rotate(double2 &a, double2 &b, double t, double s) {
+  double x = fma(t, b.y, a.x);
+  b.y = fma(-s, x, b.y);
+  a.x = fma(t, b.y, x);
+  x = fma(t, a.y, b.x);
+  a.y = fma(-s, x, a.y);
+  b.x = fma(t, a.y, x);
 }
+
 
 template <typename R, bool SITES>
 __global__ void __launch_bounds__(512)
@@ -460,15 +455,14 @@ sweep_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pdes
     const Op op = ops[d.op0 + k];
     if (op.kind == OP_GATE) {
       const GateCoef g = coefs[op.coef];
-      const R c1 = sizeof(R) == 8 ? (R)g.cm1 : (R)g.tf;
+      const R c1 = sizeof(R) == 8 ? (R)g.t : (R)g.tf;
       const R s = sizeof(R) == 8 ? (R)g.s : (R)g.sft;
       const int lo = op.u < op.v ? op.u : op.v, hi = op.u < op.v ? op.v : op.u;
       const uint32_t bu = 1u << op.u, bv = 1u << op.v;
       for (uint32_t p = tid; p < (T >> 2); p += nt) {
         const uint32_t t0 = insert_zero(insert_zero(p, lo), hi);
         C a = tile[t0 | bu], b = tile[t0 | bv];
-        if constexpr (sizeof(R) == 8) rotate<R>(a, b, c1, s);
-        else shear_rotate(a, b, c1, s);
+        shear_rotate(a, b, c1, s);
         tile[t0 | bu] = a;
         tile[t0 | bv] = b;
       }
