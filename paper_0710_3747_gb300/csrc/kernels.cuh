@@ -681,19 +681,30 @@ __device__ __forceinline__ void shear_lo_hi(u64 &P, u64 &Q, float t, float n) {
 template <int NP, int JU, int JV>
 __device__ __forceinline__ void gate_packed(u64 (&RE)[NP], u64 (&IM)[NP], float t, float s) {
   const u64 t2 = pack2(t, t), n2 = pack2(-s, -s);
+  // plane (Re a, Im b) = (RE[j], IM[k]); plane (Re b, Im a) = (RE[k], IM[j]);
+  // each shear step over every plane of the gate before the next (independent
+  // instructions back to back)
 #pragma unroll
-  for (int j = 0; j < NP; ++j) {
+  for (int j = 0; j < NP; ++j)
     if (((j >> JU) & 1) == 1 && ((j >> JV) & 1) == 0) {
       const int k = j ^ (1 << JU) ^ (1 << JV);
-      // plane (Re a, Im b) = (RE[j], IM[k]); plane (Re b, Im a) = (RE[k], IM[j])
-      fma2_acc(RE[j], t2, IM[k]);
-      fma2_acc(RE[k], t2, IM[j]);
-      fma2_acc(IM[k], n2, RE[j]);
-      fma2_acc(IM[j], n2, RE[k]);
       fma2_acc(RE[j], t2, IM[k]);
       fma2_acc(RE[k], t2, IM[j]);
     }
-  }
+#pragma unroll
+  for (int j = 0; j < NP; ++j)
+    if (((j >> JU) & 1) == 1 && ((j >> JV) & 1) == 0) {
+      const int k = j ^ (1 << JU) ^ (1 << JV);
+      fma2_acc(IM[k], n2, RE[j]);
+      fma2_acc(IM[j], n2, RE[k]);
+    }
+#pragma unroll
+  for (int j = 0; j < NP; ++j)
+    if (((j >> JU) & 1) == 1 && ((j >> JV) & 1) == 0) {
+      const int k = j ^ (1 << JU) ^ (1 << JV);
+      fma2_acc(RE[j], t2, IM[k]);
+      fma2_acc(RE[k], t2, IM[j]);
+    }
 }
 
 // Gate on the pack bit and register bit JV + 1: the pair is the high lane of
