@@ -170,3 +170,28 @@ def test_hamiltonian_families_match_oracle_convention():
     for ht in (spinrp.XY, spinrp.DIPOLAR, spinrp.ISOTROPIC):
         assert len(spinrp.System(J, ht).bonds()) == 15
     assert spinrp.System(J, spinrp.ISING).bonds() == []
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_register_programs_random_graphs(seed):
+    """Random coupling graphs (sparse to dense, with and without S^zS^z
+    terms), tile widths and register widths: the host replay of every index
+    the register-blocked kernel forms and of every register program against
+    its sweep's op list must pass (plan_check raises otherwise)."""
+    rng = np.random.default_rng([0xF022, seed])
+    M = int(rng.integers(11, 23))
+    density = float(rng.uniform(0.1, 1.0))
+    J = rng.normal(size=(M, M)) * (rng.random((M, M)) < density)
+    J = np.triu(J, 1)
+    J = J + J.T
+    J[0, 1] = J[1, 0] = 1.0  # spin 1 always coupled
+    htype = [spinrp.XY, spinrp.DIPOLAR, spinrp.ISOTROPIC][seed % 3]
+    s = spinrp.System(J, htype)
+    for K in sorted({int(rng.integers(10, min(M, 14) + 1)), min(M, 14)}):
+        for rb in (5, 6):
+            if K < 5 + rb:
+                continue
+            s.set_tile("c64", K)
+            s.set_regbits(rb)
+            st = s.plan_check("c64")
+            assert st["phases_per_sweep"] >= 1.0
