@@ -96,6 +96,34 @@ const char *spinrp_version(void);
 int spinrp_system_create(int M, const double *J, int htype, const double *a_generic,
                          spinrp_system **out);
 
+/* The paper's two coupling networks ("Spin systems with different coupling
+ * networks"), built in the library:
+ * the open two-leg ladder of M = 2L spins, legs 1..L and L+1..2L with
+ * neighbour coupling j_leg, rungs (n, n+L) with j_rung, XY Hamiltonian
+ * (a = 0, b = J; the paper's b_x = j_leg, b_y = j_rung). */
+int spinrp_ladder_create(int L, double j_leg, double j_rung, spinrp_system **out);
+
+/* The star of M spins with truncated dipolar couplings: spin 1 at the origin,
+ * spins 2..M uniform in the unit ball and at least rmin (0..0.5) apart, drawn
+ * by rejection from Philox4x32-10 with key (lo32, hi32 of geom_seed) --
+ * candidate n takes x, y from the words of counter (n, 0, 0, 2) and z from
+ * counter (n, 1, 0, 2), each the top 53 bits of two words scaled to [-1, 1);
+ * J_ij = (1 - 3 cos^2 theta_ij)/r_ij^3 (theta from the z axis) rescaled to unit
+ * rms over pairs; Hamiltonian J [2 S^zS^z - (S^xS^x + S^yS^y)] (a = 2J, b = -J,
+ * the a/b = -2 of the paper).  Errors: SPINRP_EINVAL. */
+int spinrp_star_dipolar_create(int M, uint64_t geom_seed, double rmin, spinrp_system **out);
+
+/* Copy the M x M coupling matrices of H (row-major, symmetric, zero diagonal):
+ * a (S^zS^z) and b (flip-flop); either pointer may be NULL. */
+int spinrp_system_couplings(const spinrp_system *sys, double *a, double *b);
+
+/* The order in which the evolution applies the flip-flop bonds of the
+ * forward half step, as indices into spinrp_system_bonds: 0, 1, ..., B-1.
+ * The device reorders only gates on disjoint spins (they commute exactly),
+ * so this is the product an external checker must replay.  Writes
+ * min(B, cap) indices; *n receives B. */
+int spinrp_schedule(const spinrp_system *sys, int32_t *bond_order, int cap, int *n);
+
 /* Free a system (NULL is ignored).  States created from it stay valid. */
 void spinrp_system_destroy(spinrp_system *sys);
 
@@ -117,9 +145,9 @@ int spinrp_system_set_tile(spinrp_system *sys, int prec, int K);
 
 /* Register bits per phase of the complex64 tile kernel: each thread keeps the
  * 2^rb amplitudes spanned by rb tile bits in registers while it applies every
- * ready gate on those bits (rb = 5 or 6; 0 restores the default, 5).  Wider
- * register sets apply more gates per shared-memory round trip with fewer
- * threads per tile.  The second autotuner knob; affects states and batches
+ * ready gate on those bits (rb = 5 or 6; 0 restores the default: 6 for
+ * tiles of 11+ spins, else 5).  Wider register sets apply more gates per
+ * shared-memory round trip with fewer threads per tile.  The second autotuner knob; affects states and batches
  * created afterwards.  Errors: SPINRP_EINVAL. */
 int spinrp_system_set_regbits(spinrp_system *sys, int rb);
 

@@ -111,6 +111,90 @@ extern "C" int spinrp_system_create(int M, const double *J, int htype, const dou
   return SPINRP_OK;
 }
 
+extern "C" int spinrp_ladder_create(int L, double j_leg, double j_rung, spinrp_system **out) {
+  if (L < 1 || 2 * L > kMaxM || !std::isfinite(j_leg) || !std::isfinite(j_rung))
+    return fail(SPINRP_EINVAL, "ladder_create: bad argument (L=%d)", L);
+  const int M = 2 * L;
+  std::vector<double> J((size_t)M * M, 0.0);
+  for (int k = 0; k + 1 < L; ++k) {
+    J[k * M + k + 1] = J[(k + 1) * M + k] = j_leg;                                  // leg 1..L
+    J[(L + k) * M + L + k + 1] = J[(L + k + 1) * M + L + k] = j_leg;                // leg L+1..2L
+  }
+  for (int k = 0; k < L; ++k) J[k * M + L + k] = J[(L + k) * M + k] = j_rung;  // rungs (n, n+L)
+  return spinrp_system_create(M, J.data(), SPINRP_XY, nullptr, out);
+}
+
+namespace {
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), host side: the star's
+// geometry draws.
+void host_philox(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0], p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0, n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+    c[1] = (uint32_t)p1, c[3] = (uint32_t)p0, c[0] = n0, c[2] = n2;
+    k0 += 0x9E3779B9u, k1 += 0xBB67AE85u;
+  }
+}
+// u in [0, 1) from two 32-bit words (top 53 bits)
+double host_u53(uint32_t hi, uint32_t lo) {
+  return (double)((((uint64_t)hi << 32) | lo) >> 11) * (1.0 / 9007199254740992.0);
+}
+}  // namespace
+
+extern "C" int spinrp_star_dipolar_create(int M, uint64_t geom_seed, double rmin, spinrp_system **out) {
+  if (M < 2 || M > kMaxM || !(rmin >= 0.0) || rmin > 0.5)
+    return fail(SPINRP_EINVAL, "star_dipolar_create: bad argument (M=%d, rmin=%g)", M, rmin);
+  // spin 1 at the origin; candidates n = 0, 1, ...: counter (n, 0, 0, 2)
+  // gives x, y from words (0,1), (2,3), counter (n, 1, 0, 2) gives z; a
+  // candidate outside the unit ball or closer than rmin to a kept spin is
+  // dropped
+  const uint32_t k0 = (uint32_t)geom_seed, k1 = (uint32_t)(geom_seed >> 32);
+  std::vector<double> px(1, 0.0), py(1, 0.0), pz(1, 0.0);
+  for (uint32_t n = 0; (int)px.size() < M; ++n) {
+    if (n > 100000000u) return fail(SPINRP_EINVAL, "star_dipolar_create: cannot place %d spins", M);
+    uint32_t a[4] = {n, 0u, 0u, 2u}, b[4] = {n, 1u, 0u, 2u};
+    host_philox(a, k0, k1);
+    host_philox(b, k0, k1);
+    const double x = 2.0 * host_u53(a[0], a[1]) - 1.0, y = 2.0 * host_u53(a[2], a[3]) - 1.0,
+                 z = 2.0 * host_u53(b[0], b[1]) - 1.0;
+    if (x * x + y * y + z * z > 1.0) continue;
+    bool ok = true;
+    for (size_t q = 0; q < px.size() && ok; ++q) {
+      const double dx = x - px[q], dy = y - py[q], dz = z - pz[q];
+      ok = dx * dx + dy * dy + dz * dz >= rmin * rmin;
+    }
+    if (ok) px.push_back(x), py.push_back(y), pz.push_back(z);
+  }
+  // J_ij = (1 - 3 cos^2 theta_ij) / r_ij^3 (theta from the z axis), unit rms over pairs
+  std::vector<double> J((size_t)M * M, 0.0);
+  double sum2 = 0.0;
+  for (int i = 0; i < M; ++i)
+    for (int j = i + 1; j < M; ++j) {
+      const double dx = px[i] - px[j], dy = py[i] - py[j], dz = pz[i] - pz[j];
+      const double r2 = dx * dx + dy * dy + dz * dz, r = std::sqrt(r2);
+      const double c = dz / r, v = (1.0 - 3.0 * c * c) / (r2 * r);
+      J[i * M + j] = J[j * M + i] = v;
+      sum2 += v * v;
+    }
+  const double rms = std::sqrt(sum2 / (0.5 * M * (M - 1)));
+  for (double &v : J) v /= rms;
+  return spinrp_system_create(M, J.data(), SPINRP_DIPOLAR, nullptr, out);
+}
+
+extern "C" int spinrp_system_couplings(const spinrp_system *sys, double *a, double *b) {
+  if (!sys || (!a && !b)) return fail(SPINRP_EINVAL, "system_couplings: bad argument");
+  if (a) std::copy(sys->a.begin(), sys->a.end(), a);
+  if (b) std::copy(sys->b.begin(), sys->b.end(), b);
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_schedule(const spinrp_system *sys, int32_t *bond_order, int cap, int *n) {
+  if (!sys || !n || (cap > 0 && !bond_order)) return fail(SPINRP_EINVAL, "schedule: bad argument");
+  *n = (int)sys->bonds.size();
+  for (int k = 0; k < std::min(cap, *n); ++k) bond_order[k] = k;
+  return SPINRP_OK;
+}
+
 extern "C" void spinrp_system_destroy(spinrp_system *sys) { delete sys; }
 
 extern "C" int spinrp_system_num_spins(const spinrp_system *sys) { return sys ? sys->M : 0; }

@@ -76,6 +76,12 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             "spinrp_state_destroy": ([vp], None),
             "spinrp_state_init_random_phase": ([vp, ctypes.c_uint64], ctypes.c_int),
             "spinrp_state_init_product_phase": ([vp, ctypes.c_uint64], ctypes.c_int),
+            "spinrp_ladder_create": ([ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.POINTER(vp)],
+                                     ctypes.c_int),
+            "spinrp_star_dipolar_create": ([ctypes.c_int, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(vp)],
+                                           ctypes.c_int),
+            "spinrp_system_couplings": ([vp, dp, dp], ctypes.c_int),
+            "spinrp_schedule": ([vp, i32p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "spinrp_state_set_sites": ([vp, ctypes.c_int], ctypes.c_int),
             "spinrp_site_series": ([vp, dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
             "spinrp_state_load": ([vp, dp], ctypes.c_int),
@@ -148,10 +154,49 @@ def system_create(J, htype: int, a_generic=None) -> ctypes.c_void_p:
 class System:
     """A spin system (couplings + sweep plan), host side."""
 
-    def __init__(self, J, htype: int, a_generic=None):
-        self._h = system_create(J, htype, a_generic)
-        self.J = np.array(J, dtype=np.float64)
+    def __init__(self, J, htype: int, a_generic=None, _handle=None):
+        if _handle is None:
+            self._h = system_create(J, htype, a_generic)
+            self.J = np.array(J, dtype=np.float64)
+        else:
+            self._h = _handle
+            self.J = np.array(J, dtype=np.float64)
         self.htype = int(htype)
+
+    @classmethod
+    def ladder(cls, L: int, j_leg: float = 1.0, j_rung: float = 0.5) -> "System":
+        """spinrp_ladder_create: the open 2 x L XY ladder."""
+        h = ctypes.c_void_p()
+        _check(lib().spinrp_ladder_create(int(L), float(j_leg), float(j_rung), ctypes.byref(h)))
+        sysm = cls(np.zeros((1, 1)), XY, _handle=h)
+        sysm.J = sysm.couplings()[1]
+        return sysm
+
+    @classmethod
+    def star_dipolar(cls, M: int, geom_seed: int, rmin: float = 0.1) -> "System":
+        """spinrp_star_dipolar_create: the truncated dipolar star built in the library."""
+        h = ctypes.c_void_p()
+        _check(lib().spinrp_star_dipolar_create(int(M), int(geom_seed) & (2**64 - 1), float(rmin),
+                                                ctypes.byref(h)))
+        sysm = cls(np.zeros((1, 1)), DIPOLAR, _handle=h)
+        sysm.J = -sysm.couplings()[1]  # b = -J
+        return sysm
+
+    def couplings(self) -> tuple[np.ndarray, np.ndarray]:
+        """(a, b): the S^zS^z and flip-flop coupling matrices of H."""
+        M = self.M
+        a = np.empty((M, M))
+        b = np.empty((M, M))
+        _check(lib().spinrp_system_couplings(self._h, _dp(a), _dp(b)))
+        return a, b
+
+    def schedule(self) -> list[int]:
+        """Order of the forward half step's bonds (indices into bonds())."""
+        n = ctypes.c_int()
+        _check(lib().spinrp_schedule(self._h, None, 0, ctypes.byref(n)))
+        buf = (ctypes.c_int32 * max(n.value, 1))()
+        _check(lib().spinrp_schedule(self._h, buf, n.value, ctypes.byref(n)))
+        return [buf[k] for k in range(n.value)]
 
     @property
     def handle(self):

@@ -195,3 +195,51 @@ def test_register_programs_random_graphs(seed):
             s.set_regbits(rb)
             st = s.plan_check("c64")
             assert st["phases_per_sweep"] >= 1.0
+
+
+def test_ladder_constructor_matches_definition():
+    for L, jl, jr in ((1, 1.0, 0.3), (4, 0.7, 0.2), (15, 1.0, 0.5)):
+        s = spinrp.System.ladder(L, jl, jr)
+        a, b = s.couplings()
+        assert np.array_equal(b, W.ladder(L, jl, jr)) and not a.any()
+        assert s.schedule() == list(range(len(s.bonds())))
+
+
+def _star_from_recipe(M, seed, rmin):
+    """The documented geometry recipe, replayed with the (separately pinned)
+    Philox4x32-10 of the test oracle."""
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    u = lambda hi, lo: (((hi << 32) | lo) >> 11) * 2.0 ** -53
+    pos = [np.zeros(3)]
+    n = 0
+    while len(pos) < M:
+        a = oracle.philox4x32_10((n, 0, 0, 2), key)
+        b = oracle.philox4x32_10((n, 1, 0, 2), key)
+        n += 1
+        p = np.array([2 * u(a[0], a[1]) - 1, 2 * u(a[2], a[3]) - 1, 2 * u(b[0], b[1]) - 1])
+        if p @ p > 1.0 or min(np.linalg.norm(p - q) for q in pos) < rmin:
+            continue
+        pos.append(p)
+    J = W.dipolar_from_positions(np.array(pos))
+    return J
+
+
+@pytest.mark.parametrize("M,seed,rmin", [(2, 1, 0.1), (9, 2**40 + 3, 0.1), (14, 7, 0.15)])
+def test_star_constructor_matches_recipe(M, seed, rmin):
+    s = spinrp.System.star_dipolar(M, seed, rmin)
+    a, b = s.couplings()
+    J = _star_from_recipe(M, seed, rmin)
+    np.testing.assert_allclose(-b, J, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(a, 2 * J, rtol=1e-12, atol=1e-12)
+    iu = np.triu_indices(M, 1)
+    assert abs(np.sqrt(np.mean(b[iu] ** 2)) - 1.0) < 1e-12
+    if M > 2:  # two spins: J_12 = +-1 after the rms scaling for any geometry
+        assert not np.array_equal(b, spinrp.System.star_dipolar(M, seed + 1, rmin).couplings()[1])
+
+
+def test_constructors_reject_bad_arguments():
+    for call in (lambda: spinrp.System.ladder(0), lambda: spinrp.System.ladder(18),
+                 lambda: spinrp.System.star_dipolar(1, 1), lambda: spinrp.System.star_dipolar(40, 1),
+                 lambda: spinrp.System.star_dipolar(8, 1, rmin=0.9)):
+        with pytest.raises(spinrp.SpinrpError):
+            call()

@@ -289,3 +289,19 @@ def test_ladder_m30_sampled():
         P = st.polarization()
         assert np.all(np.abs(P) <= 1.0 + 1e-6)
         st.close()
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_library_built_systems_match_oracle(prec):
+    """Systems from spinrp_ladder_create / spinrp_star_dipolar_create evolve
+    as the oracle does with the couplings the library reports."""
+    for sysm, dt in ((spinrp.System.ladder(6, 1.0, 0.3), 0.05), (spinrp.System.star_dipolar(12, 9), 0.02)):
+        a, b = sysm.couplings()
+        st = spinrp.State(sysm, prec, series_cap=31)
+        st.init_random_phase(4).evolve(dt, 30)
+        M = sysm.M
+        psi = oracle.init_random_phase(M, 4)
+        P, _ = oracle.evolve(psi, a, b, dt, 30)
+        tol = 1e-10 if prec == "c128" else 1e-4
+        assert np.max(np.abs(st.polarization()[1:] - P)) <= tol
+        st.close()
