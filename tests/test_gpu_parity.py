@@ -305,3 +305,29 @@ def test_library_built_systems_match_oracle(prec):
         tol = 1e-10 if prec == "c128" else 1e-4
         assert np.max(np.abs(st.polarization()[1:] - P)) <= tol
         st.close()
+
+
+def test_largest_state_m34():
+    """2x17 ladder at the largest supported size, 2^34 complex64 amplitudes
+    (128 GiB; offsets beyond 32 bits, 2^21 blocks per sweep): the initial
+    amplitudes at sampled indices against the oracle's phase draw, then two
+    steps forward and two back return every sampled amplitude to its start
+    (the step is a palindrome, so U(-dt) U(dt) = 1), with the norm kept."""
+    M, seed = 34, 11
+    sysm = spinrp.System.ladder(17, 1.0, 0.5)
+    st = spinrp.State(sysm, "c64", series_cap=8)
+    st.init_random_phase(seed)
+    rng = np.random.default_rng(34)
+    idx = np.concatenate([rng.integers(0, 1 << M, size=2048), [0, 1, (1 << M) - 1, (1 << M) - 2, (1 << 33) + 1]])
+    got0 = st.read(idx)
+    amp = 2.0 ** (-(M - 1) / 2)
+    want = np.array([amp * np.exp(2j * np.pi * oracle.phase_uniform(seed, int(x) >> 1)) if x & 1 else 0.0
+                     for x in idx])
+    assert np.max(np.abs(got0 - want)) < 2e-7 * amp
+    st.evolve(0.05, 2).evolve(-0.05, 2)
+    got1 = st.read(idx)
+    assert np.max(np.abs(got1 - got0)) < 1e-5 * amp
+    N = st.norm_series()
+    assert np.max(np.abs(N - 1.0)) < 1e-5
+    assert abs(st.polarization()[-1] - 1.0) < 1e-5
+    st.close()
