@@ -533,9 +533,12 @@ static Layout work_layout(int M, int nb, int64_t cap, const PassSet &ps, int max
   return L;
 }
 
-// Register-blocked tiles are used for complex64 when the tile has at least
-// 5 lane bits besides the rb register bits (2^(K-rb) threads).
-static bool use_phases(int prec, int K, int rb) { return prec == SPINRP_C64 && K >= 5 + rb; }
+// Register-blocked tiles are used when the tile has at least 5 lane bits
+// besides the rb register bits (2^(K-rb) threads); complex128 runs five
+// register bits (32 FP64 amplitudes per thread).
+static bool use_phases(int prec, int K, int rb) {
+  return prec == SPINRP_C64 ? K >= 5 + rb : (rb == 5 && K >= 10);
+}
 // Six register bits (fewer phases, so fewer shared-memory round trips per
 // gate) wherever the tile leaves five lane bits; five below that.
 static int default_regbits(int K) { return K >= 11 ? 6 : 5; }
@@ -547,9 +550,14 @@ static int default_regbits(int K) { return K >= 11 ? 6 : 5; }
 // after the gates it follows.
 constexpr int kPhaseBeam = 8;  // beam width of the phase planner
 
-static bool compile_phases(PassSet *ps, int K, int RB, std::string *err) {
+static bool compile_phases(PassSet *ps, int K, int RB, int prec, std::string *err) {
   ps->phases.clear();
   ps->rops.clear();
+  const bool wide = prec != SPINRP_C64;  // 16-byte amplitudes, swizzle_slot16
+  auto slot_of = [&](uint32_t t) { return wide ? swizzle_slot16(t) : swizzle_slot(t); };
+  // lane bits of distinct residues mod `nres` give an access group distinct
+  // banks: four (mod 4) for 8-byte amplitudes, three (mod 3) for 16-byte ones
+  const int nres = wide ? 3 : 4;
   for (PassDesc &d : ps->desc) {
     // store order: chunk-index bits 0..2 are output bits 1..3 (128-byte runs);
     // the fourth, the last lane bit of a half-warp, is the output bit whose
@@ -588,23 +596,24 @@ static bool compile_phases(PassSet *ps, int K, int RB, std::string *err) {
       memset(&ph, 0, sizeof ph);
       uint32_t isreg = 0;
       for (int k = 0; k < RB; ++k) ph.rb[k] = (uint8_t)rb[k], isreg |= 1u << rb[k];
-      // lane bits: four non-register bits of distinct residues mod 4 (bank-
-      // conflict free with the shared-memory swizzle), then the lowest left
+      // lane bits: nres non-register bits of distinct residues mod nres
+      // (bank-conflict free with the shared-memory swizzle), then the lowest left
       std::vector<int> free_bits, lanes;
       for (int b = 0; b < K; ++b)
         if (!((isreg >> b) & 1)) free_bits.push_back(b);
       uint32_t used = 0, res = 0;
       for (int b : free_bits)
-        if (lanes.size() < 4 && !((res >> (b & 3)) & 1)) lanes.push_back(b), used |= 1u << b, res |= 1u << (b & 3);
+        if ((int)lanes.size() < nres && !((res >> (b % nres)) & 1))
+          lanes.push_back(b), used |= 1u << b, res |= 1u << (b % nres);
       for (int b : free_bits)
         if (lanes.size() < 5 && !((used >> b) & 1)) lanes.push_back(b), used |= 1u << b;
       for (int k = 0; k < 5; ++k) ph.lanes[k] = (uint8_t)lanes[k];
       int nw = 0;
       for (int b : free_bits)
         if (!((used >> b) & 1)) ph.warps[nw++] = (uint8_t)b;
-      for (int k = 0; k < RB; ++k) ph.sm[k] = (uint16_t)swizzle_slot(1u << ph.rb[k]);
-      for (int k = 0; k < 5; ++k) ph.tslot[k] = (uint16_t)swizzle_slot(1u << ph.lanes[k]);
-      for (int k = 0; k < K - RB - 5; ++k) ph.tslot[5 + k] = (uint16_t)swizzle_slot(1u << ph.warps[k]);
+      for (int k = 0; k < RB; ++k) ph.sm[k] = (uint16_t)slot_of(1u << ph.rb[k]);
+      for (int k = 0; k < 5; ++k) ph.tslot[k] = (uint16_t)slot_of(1u << ph.lanes[k]);
+      for (int k = 0; k < K - RB - 5; ++k) ph.tslot[5 + k] = (uint16_t)slot_of(1u << ph.warps[k]);
       ph.op0 = (int)ps->rops.size();
       ph.nops = 0;
       for (const ROp &r : pending) ps->rops.push_back(r), ph.nops++;
@@ -714,11 +723,11 @@ static int plan_state(const spinrp_system &sys, int prec, Plan *plan, PassSet *p
   if (rc) return rc;
   build_passes(*plan, any_diag(sys), ps);
   ps->phased = false;
-  ps->rb = sys.regbits ? sys.regbits : default_regbits(plan->K);
+  ps->rb = prec != SPINRP_C64 ? 5 : sys.regbits ? sys.regbits : default_regbits(plan->K);
   if (use_phases(prec, plan->K, ps->rb)) {
     // a program too large to stage in shared memory runs the plain kernel
     std::string err;
-    ps->phased = compile_phases(ps, plan->K, ps->rb, &err);
+    ps->phased = compile_phases(ps, plan->K, ps->rb, prec, &err);
     if (!ps->phased) ps->phases.clear(), ps->rops.clear();
   }
   // every gate on two distinct bits of its tile; every store permutation a permutation
@@ -777,23 +786,27 @@ static int set_smem_limits() {
     CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
     CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<5, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
     CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
+  } else {
+    CUDA_TRY(cudaFuncSetAttribute(sweep2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 << 13));
   }
   return SPINRP_OK;
 }
 
 // Register-blocked sweep blocks resident on the whole device at once (the L2
 // prefetch distance); 0 when the query fails.
-static unsigned sweep2_resident(int rb, int K) {
+static unsigned sweep2_resident(int prec, int rb, int K) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  const size_t smem = size_t(8) << K;
+  const size_t smem = (prec == SPINRP_C64 ? size_t(8) : size_t(16)) << K;
   const cudaError_t e =
-      rb == 6 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep2_kernel<6, false>, 1 << (K - 6), smem)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep2_kernel<5, false>, 1 << (K - 5), smem);
+      prec != SPINRP_C64
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep2d_kernel, 1 << (K - 5), smem)
+      : rb == 6 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep2_kernel<6, false>, 1 << (K - 6), smem)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep2_kernel<5, false>, 1 << (K - 5), smem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -912,7 +925,7 @@ extern "C" int spinrp_state_create(const spinrp_system *sys, int prec, void *str
     free_state(st);
     return rc;
   }
-  if (st->ps.phased) st->prefetch_ahead = sweep2_resident(st->ps.rb, st->plan.K);
+  if (st->ps.phased) st->prefetch_ahead = sweep2_resident(prec, st->ps.rb, st->plan.K);
   *out = st;
   return SPINRP_OK;
 }
@@ -1114,6 +1127,10 @@ static int launch_pass(const LaunchCtx &c, int pass, cudaStream_t stream, bool l
       sweep2_kernel<5, false><<<grid, 1 << (K - 5), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M,
                                                                         ahead);
   }
+  else if (sizeof(R) == 8 && c.v2 && !c.sites)
+    // complex128 register-blocked (the all-site readout runs the plain kernel)
+    sweep2d_kernel<<<grid, 1 << (K - 5), smem, stream>>>(c.jobs, c.ps->desc[pass], c.phases, c.rops, c.M,
+                                                          c.prefetch_ahead);
   else if (c.sites)
     sweep_kernel<R, true><<<grid, nt, smem, stream>>>(c.jobs, c.passes + pass, c.ops, c.M);
   else
@@ -1295,7 +1312,7 @@ extern "C" int spinrp_evolve(spinrp_state *st, double dt, int64_t steps, int ord
       coef_kernel<<<(2 * st->nb + 127) / 128, 128, 0, st->stream>>>(st->d_job, st->nb, dt);
       CUDA_TRY(cudaGetLastError());
     }
-    if (st->v2 && !st->ps.rops.empty()) {
+    if (st->v2 && st->prec == SPINRP_C64 && !st->ps.rops.empty()) {
       const int nr = (int)st->ps.rops.size();
       ++g_launches;
       resolve_ops_kernel<<<(nr + 127) / 128, 128, 0, st->stream>>>(st->d_job, st->rops, nr);
@@ -1587,6 +1604,133 @@ std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint
   }
   return "";
 }
+
+// Host replay of sweep2d_kernel's (complex128) index arithmetic for one pass
+// and one block, as audit_sweep2 does for the complex64 kernel: one 16-byte
+// amplitude per access, 32 amplitudes per thread, slots by swizzle_slot16.
+std::string audit_sweep2d(const PassDesc &d, const PhaseDesc *phases, int M, uint64_t block,
+                          size_t nphases_all, size_t nrops_all) {
+  constexpr int rb = 5;
+  const int K = d.K, nt = 1 << (K - rb), lognt = K - rb;
+  if (K < 10 || K > 13) return "tile width outside 10..13";
+  if (d.nphases < 0 || d.nphases > kMaxPassPhases || d.nrops < 0 || d.nrops > kMaxPassOps ||
+      d.phase0 < 0 || (size_t)d.phase0 + d.nphases > nphases_all || d.rop0 < 0 ||
+      (size_t)d.rop0 + d.nrops > nrops_all)
+    return "program staging out of range";
+  for (int p = 0; p < d.nphases; ++p) {
+    const int o0 = phases[d.phase0 + p].op0 - d.rop0;
+    if (o0 < 0 || o0 + phases[d.phase0 + p].nops > d.nrops) return "phase op range";
+  }
+  if (M - K > 31) return "more than 31 outer bits";
+  const uint32_t T = 1u << K;
+  uint64_t base = 0;
+  for (int k = 0; k < M - K; ++k) base |= ((block >> k) & 1ull) << d.outer_pos[k];
+  auto phys = [&](uint32_t t) {
+    uint64_t o = base;
+    for (int q = 0; q < K; ++q) o |= (uint64_t)((t >> q) & 1u) << d.tile_pos[q];
+    return o;
+  };
+  const uint64_t N = 1ull << M;
+  char buf[160];
+  auto gray = [](int g) { return g ^ (g >> 1); };
+  auto low_bit = [](int g) { int k = 0; while (!((g >> k) & 1)) ++k; return k; };
+  // load: amplitude t = tid + nt*gray(g), runs of eight from the origin
+  std::vector<char> seen(T, 0);
+  for (int tid = 0; tid < nt; ++tid) {
+    uint64_t off = 0;
+    for (int k = 0; k < lognt; ++k) if ((tid >> k) & 1) off |= 1ull << d.tile_pos[k];
+    const int64_t elem0 = (int64_t)(base + off);
+    const uint32_t s0 = swizzle_slot16((uint32_t)tid);
+    int64_t elem = elem0;
+    uint32_t sl = s0;
+    for (int g = 0; g < (1 << rb); ++g) {
+      if ((g & 7) == 0) {
+        elem = elem0, sl = s0;
+        for (int k = 0; k < rb; ++k)
+          if ((gray(g) >> k) & 1)
+            elem += (int64_t)1 << d.tile_pos[lognt + k], sl ^= swizzle_slot16(1u << (lognt + k));
+      } else {
+        const int k = low_bit(g);
+        const int64_t dg = (int64_t)1 << d.tile_pos[lognt + k];
+        elem += ((gray(g) >> k) & 1) ? dg : -dg;
+        sl ^= swizzle_slot16(1u << (lognt + k));
+      }
+      const uint32_t t = ((uint32_t)gray(g) << lognt) | (uint32_t)tid;
+      if (t >= T || sl >= T || sl != swizzle_slot16(t) || seen[sl]++ || elem < 0 || (uint64_t)elem >= N ||
+          (uint64_t)elem != phys(t)) {
+        snprintf(buf, sizeof buf, "load index out of place (t=%u)", t);
+        return buf;
+      }
+    }
+  }
+  // phases: each thread's 32-amplitude subcube and the kernel's walk over it
+  for (int p = 0; p < d.nphases; ++p) {
+    const PhaseDesc &ph = phases[d.phase0 + p];
+    std::fill(seen.begin(), seen.end(), 0);
+    for (int tid = 0; tid < nt; ++tid) {
+      uint32_t t0 = 0;
+      for (int k = 0; k < 5; ++k) t0 |= ((uint32_t)(tid >> k) & 1u) << ph.lanes[k];
+      for (int k = 0; k < lognt - 5; ++k) t0 |= ((uint32_t)(tid >> (5 + k)) & 1u) << ph.warps[k];
+      uint32_t s0 = 0;
+      for (int b = 0; b < lognt; ++b)
+        if ((tid >> b) & 1) s0 ^= ph.tslot[b];
+      const uint32_t ob = s0 << 4;
+      uint32_t o = ob;
+      for (int g = 0; g < (1 << rb); ++g) {
+        const int j = gray(g);
+        if ((g & 7) == 0) {
+          o = ob;
+          for (int k = 0; k < rb; ++k)
+            if ((j >> k) & 1) o ^= (uint32_t)ph.sm[k] << 4;
+        } else {
+          o ^= (uint32_t)ph.sm[low_bit(g)] << 4;
+        }
+        uint32_t t = t0;
+        for (int k = 0; k < rb; ++k)
+          if ((j >> k) & 1) t |= 1u << ph.rb[k];
+        if (t >= T || (o & 15u) || (o >> 4) >= T || (o >> 4) != swizzle_slot16(t) || seen[o >> 4]++) {
+          snprintf(buf, sizeof buf, "phase %d subcube index out of place (t=%u)", p, t);
+          return buf;
+        }
+      }
+    }
+  }
+  // store: output amplitude tout = tid + nt*gray(g) takes input tile index
+  // sum of bits perm[q]
+  std::fill(seen.begin(), seen.end(), 0);
+  for (int tid = 0; tid < nt; ++tid) {
+    uint64_t off_lo = 0;
+    uint32_t pin_lo = 0;
+    for (int k = 0; k < lognt; ++k)
+      if ((tid >> k) & 1) off_lo |= 1ull << d.tile_pos[k], pin_lo |= 1u << d.perm[k];
+    const int64_t elem0 = (int64_t)(base + off_lo);
+    const uint32_t so0 = swizzle_slot16(pin_lo);
+    int64_t elem = elem0;
+    uint32_t so = so0;
+    for (int g = 0; g < (1 << rb); ++g) {
+      if ((g & 7) == 0) {
+        elem = elem0, so = so0;
+        for (int k = 0; k < rb; ++k)
+          if ((gray(g) >> k) & 1)
+            elem += (int64_t)1 << d.tile_pos[lognt + k], so ^= swizzle_slot16(1u << d.perm[lognt + k]);
+      } else {
+        const int k = low_bit(g);
+        const int64_t dh = (int64_t)1 << d.tile_pos[lognt + k];
+        elem += ((gray(g) >> k) & 1) ? dh : -dh;
+        so ^= swizzle_slot16(1u << d.perm[lognt + k]);
+      }
+      const uint32_t tout = ((uint32_t)gray(g) << lognt) | (uint32_t)tid;
+      uint32_t tin = 0;
+      for (int q = 0; q < K; ++q) tin |= ((tout >> q) & 1u) << d.perm[q];
+      if (elem < 0 || (uint64_t)elem >= N || (uint64_t)elem != phys(tout) || tin >= T ||
+          so != swizzle_slot16(tin) || seen[so]++) {
+        snprintf(buf, sizeof buf, "store index out of place (t=%u)", tout);
+        return buf;
+      }
+    }
+  }
+  return "";
+}
 }  // namespace
 
 extern "C" int spinrp_system_plan_check(const spinrp_system *sys, int prec, double *phases_per_sweep,
@@ -1610,8 +1754,10 @@ extern "C" int spinrp_system_plan_check(const spinrp_system *sys, int prec, doub
     const PassDesc &d = ps.desc[pi];
     const uint64_t nblocks = 1ull << (plan.M - K);
     for (uint64_t blk : {uint64_t(0), nblocks / 3, nblocks - 1}) {
-      const std::string e = audit_sweep2(d, ps.phases.data(), plan.M, blk, ps.rb, ps.phases.size(),
-                                         ps.rops.size());
+      const std::string e =
+          prec == SPINRP_C64
+              ? audit_sweep2(d, ps.phases.data(), plan.M, blk, ps.rb, ps.phases.size(), ps.rops.size())
+              : audit_sweep2d(d, ps.phases.data(), plan.M, blk, ps.phases.size(), ps.rops.size());
       if (!e.empty()) return fail(SPINRP_EINVAL, "plan_check: pass %zu block %llu: %s", pi,
                                   (unsigned long long)blk, e.c_str());
     }
@@ -1888,7 +2034,7 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
     return rc;
   }
   for (BatchGroup &g : b->groups)
-    if (g.ps.phased) g.ctx.prefetch_ahead = sweep2_resident(g.ps.rb, g.plan.K);
+    if (g.ps.phased) g.ctx.prefetch_ahead = sweep2_resident(prec, g.ps.rb, g.plan.K);
   *out = b;
   return SPINRP_OK;
 }
@@ -1949,7 +2095,7 @@ extern "C" int spinrp_batch_evolve(spinrp_batch *b, double dt, int64_t steps, in
         coef_kernel<<<dim3((2 * g.nb + 127) / 128, n), 128, 0, b->stream>>>(g.d_jobs, g.nb, dt);
         CUDA_TRY(cudaGetLastError());
       }
-      if (g.ps.phased && !g.ps.rops.empty()) {
+      if (g.ps.phased && b->prec == SPINRP_C64 && !g.ps.rops.empty()) {
         const int nr = (int)g.ps.rops.size();
         ++g_launches;
         resolve_ops_kernel<<<dim3((nr + 127) / 128, n), 128, 0, b->stream>>>(g.d_jobs, g.ctx.rops, nr);

@@ -43,17 +43,17 @@ struct PassDesc {
   uint8_t perm[kMaxK];  // store: output tile bit q takes the amplitude bit of input tile bit perm[q]
   uint8_t tile_spin[kMaxK];   // logical spin (0-based) at each tile bit, input layout
   uint8_t outer_spin[kMaxM];  // logical spin at each outer bit, input layout
-  int32_t phase0;       // register-blocked program (complex64 path): first phase
+  int32_t phase0;       // register-blocked program: first phase
   int32_t nphases;      //   and number of phases,
   int32_t rop0;         //   first op
   int32_t nrops;        //   and number of ops
   uint8_t store_bit[kMaxK];  // store: output tile bit (1..K-1) of each chunk-index bit
 };
 
-// Register-blocked execution of a pass (complex64 path).  In a phase every
-// thread holds the 2^RB amplitudes of the tile that differ only in the RB
-// tile bits rb[] (its "subcube"; RB = 5 or 6 per plan), applies the phase's
-// ops to them in registers and writes them back to shared memory.
+// Register-blocked execution of a pass.  In a phase every thread holds the
+// 2^RB amplitudes of the tile that differ only in the RB tile bits rb[] (its
+// "subcube"; RB = 5 or 6 per plan for complex64, 5 for complex128), applies
+// the phase's ops to them in registers and writes them back to shared memory.
 // lanes[]/warps[] give the tile bits the thread index supplies.
 constexpr int kMaxRegBits = 6;  // 5 or 6 register bits per phase
 struct PhaseDesc {
@@ -76,6 +76,9 @@ constexpr int kMaxPassOps = 768;
 // Shared-memory slot of tile index t in the register-blocked kernel: the low
 // four bits are XORed with bits 4-7, 8-11 and 12-15 (XOR-linear).
 inline uint32_t swizzle_slot(uint32_t t) { return t ^ (((t >> 4) ^ (t >> 8) ^ (t >> 12)) & 15u); }
+// The complex128 kernel's slot, in 16-byte units: the low three bits are
+// XORed with bits 3-5, 6-8, 9-11 and 12-14 (XOR-linear).
+inline uint32_t swizzle_slot16(uint32_t t) { return t ^ (((t >> 3) ^ (t >> 6) ^ (t >> 9) ^ (t >> 12)) & 7u); }
 
 // Op of a phase: GATE acts on register bits given by `combo` (index of the
 // pair (ku < kv) among the RB(RB-1)/2 pairs, lexicographic); DIAG / REDUCE as

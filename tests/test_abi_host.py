@@ -122,6 +122,23 @@ def test_register_phase_programs(name, J, htype, a, K):
             assert 1.0 <= st["gates_per_phase"] <= 10.0
 
 
+@pytest.mark.parametrize("K", [10, 11, 12, 13])
+@pytest.mark.parametrize("name,J,htype,a", _systems(), ids=lambda v: v if isinstance(v, str) else "")
+def test_register_phase_programs_c128(name, J, htype, a, K):
+    """The complex128 register-blocked programs (five register bits, 16-byte
+    slots): every index the kernel forms, replayed on the host, and every
+    program against its sweep's plain op list."""
+    s = spinrp.System(J, htype, a)
+    s.set_tile("c128", K)
+    st = s.plan_check("c128")
+    if s.M >= 10:
+        assert st["phases_per_sweep"] >= 1.0
+        if s.bonds():
+            assert 1.0 <= st["gates_per_phase"] <= 10.0
+    else:
+        assert st["phases_per_sweep"] == 0.0  # tiles below 10 bits run the plain kernel
+
+
 def test_plan_sweep_counts():
     # 2x15 ladder, 13-spin tiles (the default for 2^30 complex64 amplitudes)
     # sharing 4 low bits: three segments -> four sweeps per step; the same at 14
@@ -195,6 +212,9 @@ def test_register_programs_random_graphs(seed):
             s.set_regbits(rb)
             st = s.plan_check("c64")
             assert st["phases_per_sweep"] >= 1.0
+        if K <= 13:
+            s.set_tile("c128", K)
+            assert s.plan_check("c128")["phases_per_sweep"] >= 1.0
 
 
 def test_ladder_constructor_matches_definition():
