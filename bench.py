@@ -338,7 +338,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "kernel": ("sweep2_kernel" if info["K"] >= 10 else "sweep_kernel<float>") if prec == "c64"
-                else "sweep_kernel<double>",
+                else ("sweep2d_kernel" if info["K"] >= 10 else "sweep_kernel<double>"),
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
                 "launches": sweep_n, "mean_launch_ms": sweep_avg_s * 1e3,
                 "sweep_share_of_job": sweep_ms / (ms * args.steps)}
@@ -402,9 +402,22 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         ms64 = f0.elapsed_time(f1)
         P64 = st64.polarization()
         n = min(len(P64), len(P32))
-        out["fp64"] = {"value": world * updates_per_job(job.M, nb, args.fp64_steps) / (ms64 / 1e3),
+        upd64 = updates_per_job(job.M, nb, args.fp64_steps)
+        # FP64-pipe roofline: a gate rotates 2^M / 4 flip-flop pairs at 6 FMAs
+        # each, 1.5 FMA = 3 FLOP per amplitude update; peak = SMs x max SM
+        # clock x 2 FP64 FMA per SM per clock x 2 FLOP
+        sms = torch.cuda.get_device_properties(stream.device).multi_processor_count
+        peak64 = sms * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 * 2 * 2 / 1e12
+        ach64 = 3.0 * upd64 / (ms64 / 1e3) / 1e12
+        out["fp64"] = {"value": world * upd64 / (ms64 / 1e3),
                        "unit": UNIT, "trotter_steps": args.fp64_steps, "ms": ms64,
-                       "fp32_vs_fp64_max_dP": float(np.max(np.abs(P32[:n] - P64[:n])))}
+                       "fp32_vs_fp64_max_dP": float(np.max(np.abs(P32[:n] - P64[:n]))),
+                       "roofline": {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
+                                    "frac": ach64 / peak64, "traffic": None,
+                                    "kernel": ("sweep2d_kernel" if sysm.plan_info("c128")["K"] >= 10
+                                               else "sweep_kernel<double>"),
+                                    "peak_source": "derived: SMs x max SM clock x 2 FP64 FMA/clk/SM x 2",
+                                    "flops": "flip-flop gate FMAs only"}}
         st64.close()
 
     if rank == 0 and not args.skip_cpu:

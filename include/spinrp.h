@@ -148,7 +148,9 @@ int spinrp_system_set_tile(spinrp_system *sys, int prec, int K);
  * ready gate on those bits (rb = 5 or 6; 0 restores the default: 6 for
  * tiles of 11+ spins, else 5).  Wider register sets apply more gates per
  * shared-memory round trip with fewer threads per tile.  The second autotuner knob; affects states and batches
- * created afterwards.  Errors: SPINRP_EINVAL. */
+ * created afterwards.  The complex128 tile kernel always keeps 2^5 amplitudes
+ * per thread (tiles of 10+ spins; narrower tiles run the per-gate kernel).
+ * Errors: SPINRP_EINVAL. */
 int spinrp_system_set_regbits(spinrp_system *sys, int rb);
 
 /* Describe the sweep plan the library would use for precision prec: number

@@ -15,6 +15,7 @@
 #include "../../include/spinrp.h"
 #include "internal.h"
 #include "kernels.cuh"
+#include "sweep2d.cuh"
 
 using namespace spinrp;
 
@@ -212,9 +213,11 @@ extern "C" int spinrp_system_bonds(const spinrp_system *sys, int32_t *pairs, int
 // Default tile width.  complex64: 2^14 amplitudes (128 KiB, one tile per SM)
 // while the state fits in L2 and the sweep is bound by the in-tile work; 2^13
 // (64 KiB, two tiles per SM, one loading while the other computes) for states
-// streamed from HBM.  complex128: 2^13 (128 KiB).
+// streamed from HBM.  complex128: 2^12 (64 KiB, two tiles per SM; the FP64
+// sweep is bound by the FP64 pipe, and a second resident tile covers the
+// other's loads, stores and barriers).
 static int default_K(int prec, int M) {
-  if (prec != SPINRP_C64) return 13;
+  if (prec != SPINRP_C64) return 12;
   return M >= 25 ? 13 : 14;
 }
 static int low_bits(int prec) { return prec == SPINRP_C64 ? 4 : 3; }  // 128-byte runs
