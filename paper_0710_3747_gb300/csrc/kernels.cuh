@@ -3,12 +3,14 @@
 //   init_kernel   : the paper's entangled random-phase state (or its product
 //                   state), phases from an in-kernel Philox4x32-10, fused
 //                   P(0)/norm reduction.
-//   coef_kernel   : FP64 generation of every flip-flop gate's (cos-1, sin) pair
-//                   for dt/2 and dt, rounded to FP32 with a unitarity-defect search.
+//   coef_kernel   : FP64 generation of every flip-flop gate's three-shear
+//                   coefficients (tan theta/2, sin theta) for dt/2 and dt, and
+//                   the FP32 pair closest to a rotation.
 //   diag_kernel   : FP64 -> 64-bit fixed-point turn tables of e^{-i tau a_ij/4 s s}.
 //   sweep_kernel  : one pass over the whole state in shared-memory tiles of 2^K
 //                   amplitudes: applies the pass's gates, the diagonal phase and
 //                   the polarization reduction, then writes the tile back.
+//   sweep2_kernel : the same pass with register-blocked phases (complex64).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -783,120 +785,94 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-}  // namespace sw2
 
-// Register-blocked sweep with RB register bits (2^RB amplitudes per thread,
-// 2^(K-RB) threads per tile).
-template <int RB, bool SITES>
-__global__ void __launch_bounds__(RB == 5 ? 512 : 256)
-sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops1,
-              const __grid_constant__ PassDesc d, const PhaseDesc *__restrict__ phases, int M,
-              unsigned ahead) {
-  using sw2::u64;
+// Barrier of the threads a tile's phases run on (the whole block).
+struct SyncBlock {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// Origin of tile `blk` of a pass: lane k places bit k of the tile index at
+// outer_pos[k] (M - K < 32 outer bits), a warp OR-reduction assembles the
+// offset.  Called by whole warps.
+__device__ __forceinline__ uint64_t tile_origin(unsigned blk, const PassDesc &d, int M) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t c = lane < M - d.K ? (uint64_t)((blk >> lane) & 1u) << d.outer_pos[lane] : 0ull;
+  const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)c);
+  const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(c >> 32));
+  return ((uint64_t)hi << 32) | lo;
+}
+
+// Global -> shared copy of a tile by the 2^lognt threads tid of its group
+// (8-byte async copies; 16 consecutive threads read one 128-byte run).
+// Input amplitude a = tid + nt * e: tile bits 0..lognt-1 from tid, the RB high
+// bits from e, e walked in Gray-code order in runs of eight: each copy moves
+// the source by +-2^tile_pos (a compile-time sign) and the destination slot by
+// one XOR (the slot is XOR-linear); each run starts afresh from the thread's
+// origin, so the address chains stay short.
+template <int RB>
+__device__ __forceinline__ void load_tile(const float2 *psi, uint64_t base, const PassDesc &d, int tid,
+                                          int lognt, uint32_t sbase) {
+  constexpr int NA = 1 << RB;
+  uint64_t off_amp_lo = 0;
+  for (int k = 0; k < lognt; ++k)
+    if ((tid >> k) & 1) off_amp_lo |= 1ull << d.tile_pos[k];
+  int64_t dg[RB];
+  uint32_t ds[RB];
+#pragma unroll
+  for (int k = 0; k < RB; ++k) {
+    dg[k] = (int64_t)8 << d.tile_pos[lognt + k];
+    ds[k] = slot(1u << (lognt + k)) << 3;
+  }
+  const char *src0 = reinterpret_cast<const char *>(psi + base + off_amp_lo);
+  const uint32_t sb0 = slot((uint32_t)tid) << 3;
+  const char *src = src0;
+  uint32_t sb = sb0;
+#pragma unroll
+  for (int g = 0; g < NA; ++g) {
+    if ((g & 7) == 0) {
+      src = src0, sb = sb0;
+#pragma unroll
+      for (int k = 0; k < RB; ++k)
+        if (((g ^ (g >> 1)) >> k) & 1) src += dg[k], sb ^= ds[k];
+    } else {
+      const int k = ctz6(g);
+      src += gray_up(g) ? dg[k] : -dg[k];
+      sb ^= ds[k];
+    }
+    cp_async8(sbase + sb, src);
+  }
+}
+
+// L2 prefetch of the tile at origin base2: one 128-byte run (tile bits 0..3,
+// the low physical bits) per request; run r = tid + nt * i (tile bits 4.. of
+// its first amplitude): bits from tid once, then the RB - 4 high bits per run.
+template <int RB>
+__device__ __forceinline__ void prefetch_tile(const float2 *psi, uint64_t base2, const PassDesc &d, int tid,
+                                              int lognt) {
+  uint64_t ot = base2;
+  for (int b = 0; b < lognt; ++b)
+    if ((tid >> b) & 1) ot |= 1ull << d.tile_pos[4 + b];
+#pragma unroll
+  for (int i = 0; i < (1 << (RB - 4)); ++i) {
+    uint64_t off = ot;
+#pragma unroll
+    for (int b = 0; b < RB - 4; ++b)
+      if ((i >> b) & 1) off |= 1ull << d.tile_pos[4 + lognt + b];
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(psi + off));
+  }
+}
+
+// The pass's phases on one tile in shared memory, run by the 2^lognt threads
+// tid of its group; `sync` is the group's barrier, sH/sQ/sOut the group's
+// diagonal-phase scratch, s_w the all-site scratch (SITES only).
+template <int RB, bool SITES, typename Sync>
+__device__ __forceinline__ void run_phases(float2 *tile2, const PassDesc &d, const PhaseDesc *s_ph,
+                                           const ROpRes *s_op, uint64_t base, int tid, int lognt, int M,
+                                           const uint64_t *__restrict__ qdiag, float &up, float &dn,
+                                           uint64_t *sH, uint64_t *sQ, uint64_t *sOut, double *s_w,
+                                           Sync sync) {
   constexpr int NA = 1 << RB, NP = NA / 2;
-  // one job (gridDim.y == 1): its amplitude and op arrays come with the launch
-  // so the tile copies can start at once; the rest of the job's pointers
-  // (and everything for a batch) from the job table
-  const bool one = gridDim.y == 1;
-  const JobPtrs jp = jobs[blockIdx.y];
-  float2 *__restrict__ psi = one ? psi1 : static_cast<float2 *>(jp.psi);
-  const uint64_t *__restrict__ qdiag = jp.qdiag;
-  extern __shared__ __align__(16) float2 tile2[];
-  __shared__ uint64_t sH[kMaxK];
-  __shared__ uint64_t sQ[kMaxK * kMaxK];
-  __shared__ uint64_t sOut;
-  __shared__ __align__(16) PhaseDesc s_ph[kMaxPassPhases];
-  __shared__ __align__(16) ROpRes s_op[kMaxPassOps];
-  __shared__ double s_w[SITES ? kMaxWarps * kSiteSlots : 1];
-  const int K = d.K, tid = threadIdx.x, nt = blockDim.x;
-  const int lognt = K - RB;
-  // block origin: lane k places bit k of the block index at outer_pos[k]
-  // (M - K < 32 outer bits), a warp OR-reduction assembles the offset
-  uint64_t base;
-  {
-    const int lane = tid & 31;
-    const uint64_t c = lane < M - K ? (uint64_t)((blockIdx.x >> lane) & 1u) << d.outer_pos[lane] : 0ull;
-    const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)c);
-    const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(c >> 32));
-    base = ((uint64_t)hi << 32) | lo;
-  }
-
-  // ---- global -> shared (8-byte async copies; 16 consecutive threads read
-  // one 128-byte run), issued first.  Input amplitude a = tid + nt * e: tile
-  // bits 0..lognt-1 from tid, the RB high bits from e, e walked in Gray-code
-  // order in runs of eight: each copy moves the source by +-2^tile_pos (a
-  // compile-time sign) and the destination slot by one XOR (the slot is
-  // XOR-linear); each run starts afresh from the thread's origin, so the
-  // address chains stay short.
-  {
-    uint64_t off_amp_lo = 0;
-    for (int k = 0; k < lognt; ++k)
-      if ((tid >> k) & 1) off_amp_lo |= 1ull << d.tile_pos[k];
-    int64_t dg[RB];
-    uint32_t ds[RB];
-#pragma unroll
-    for (int k = 0; k < RB; ++k) {
-      dg[k] = (int64_t)8 << d.tile_pos[lognt + k];
-      ds[k] = sw2::slot(1u << (lognt + k)) << 3;
-    }
-    const char *src0 = reinterpret_cast<const char *>(psi + base + off_amp_lo);
-    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tile2);
-    const uint32_t sb0 = sw2::slot((uint32_t)tid) << 3;
-    const char *src = src0;
-    uint32_t sb = sb0;
-#pragma unroll
-    for (int g = 0; g < NA; ++g) {
-      if ((g & 7) == 0) {
-        src = src0, sb = sb0;
-#pragma unroll
-        for (int k = 0; k < RB; ++k)
-          if (((g ^ (g >> 1)) >> k) & 1) src += dg[k], sb ^= ds[k];
-      } else {
-        const int k = sw2::ctz6(g);
-        src += sw2::gray_up(g) ? dg[k] : -dg[k];
-        sb ^= ds[k];
-      }
-      sw2::cp_async8(sbase + sb, src);
-    }
-  }
-  // the pass's program, with coefficients already resolved for this dt
-  {
-    const uint32_t *pw = reinterpret_cast<const uint32_t *>(phases + d.phase0);
-    const uint32_t a_ph = (uint32_t)__cvta_generic_to_shared(s_ph);
-    const int nw = d.nphases * (int)(sizeof(PhaseDesc) / 4);
-    for (int i = tid; i < nw; i += nt) sw2::cp_async4(a_ph + 4u * i, pw + i);
-    const ROpRes *so = (one ? sops1 : jp.sops) + d.rop0;
-    const uint32_t a_op = (uint32_t)__cvta_generic_to_shared(s_op);
-    for (int i = tid; i < d.nrops; i += nt) sw2::cp_async16(a_op + 16u * i, so + i);
-  }
-  // L2 prefetch of the tile of block blockIdx.x + ahead (ahead = blocks
-  // resident at once): DRAM keeps streaming while tiles compute, and that
-  // block's copies find its tile in L2.  One 128-byte run (tile bits 0..3,
-  // the low physical bits) per request.
-  if (ahead && blockIdx.x + ahead < gridDim.x) {
-    const unsigned pb = blockIdx.x + ahead;
-    const int lane = tid & 31;
-    const uint64_t c = lane < M - K ? (uint64_t)((pb >> lane) & 1u) << d.outer_pos[lane] : 0ull;
-    const uint64_t base2 = ((uint64_t)__reduce_or_sync(0xffffffffu, (uint32_t)(c >> 32)) << 32) |
-                           __reduce_or_sync(0xffffffffu, (uint32_t)c);
-    // run r = tid + nt * i (tile bits 4.. of its first amplitude): bits from
-    // tid once, then the RB - 4 high bits per run
-    uint64_t ot = base2;
-    for (int b = 0; b < lognt; ++b)
-      if ((tid >> b) & 1) ot |= 1ull << d.tile_pos[4 + b];
-#pragma unroll
-    for (int i = 0; i < (1 << (RB - 4)); ++i) {
-      uint64_t off = ot;
-#pragma unroll
-      for (int b = 0; b < RB - 4; ++b)
-        if ((i >> b) & 1) off |= 1ull << d.tile_pos[4 + lognt + b];
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(psi + off));
-    }
-  }
-  sw2::cp_async_wait_all();
-  __syncthreads();
-
-  float up = 0.f, dn = 0.f;
+  const int K = d.K, nt = 1 << lognt;
   const int nout = M - K;
   for (int p = 0; p < d.nphases; ++p) {
     const PhaseDesc &ph = s_ph[p];
@@ -934,14 +910,14 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops
             const uint64_t v = q[pa * M + pb];
             s += (((base >> pa) ^ (base >> pb)) & 1ull) ? (0ull - v) : v;
           }
-        sOut = s;
+        *sOut = s;
       }
       for (int w = tid; w < K * K; w += nt) sQ[w] = q[d.tile_pos[w / K] * M + d.tile_pos[w % K]];
-      __syncthreads();
+      sync();
       uint32_t isreg = 0;
       for (int k = 0; k < RB; ++k) isreg |= 1u << ph.rb[k];
       // fixed part (tile bits from the thread index) once per thread
-      uint64_t th0 = sOut;
+      uint64_t th0 = *sOut;
       for (int x = 0; x < K; ++x) {
         if ((isreg >> x) & 1u) continue;
         const uint32_t bx = (t0 >> x) & 1u;
@@ -990,7 +966,7 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops
 #pragma unroll
       for (int g = 0; g < NA; ++g) {
         if (g) {
-          const int k = sw2::ctz6(g);
+          const int k = ctz6(g);
           // sigma_k before the flip: +1 when the bit is set in gray(g - 1)
           const bool was_up = ((((g - 1) ^ ((g - 1) >> 1)) >> k) & 1) != 0;
           th += was_up ? (0ull - 2ull * F[k]) : 2ull * F[k];
@@ -1001,7 +977,7 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops
         }
         tile2[s] = cmul(tile2[s], cis_turns(th, 0.0f));
       }
-      __syncthreads();
+      sync();
       continue;
     }
     // load the subcube as NP packs, walking the packs in Gray-code order so
@@ -1023,20 +999,20 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops
           for (int k = 0; k < RB - 1; ++k)
             if ((j >> k) & 1) o ^= mb[1 + k];
         } else {
-          o ^= mb[1 + sw2::ctz5(g)];
+          o ^= mb[1 + ctz5(g)];
         }
         const uint32_t o1 = o ^ mb[0];
         const float2 v0 = *reinterpret_cast<const float2 *>(tb + o);
         const float2 v1 = *reinterpret_cast<const float2 *>(tb + o1);
-        RE[j] = sw2::pack2(v0.x, v1.x);
-        IM[j] = sw2::pack2(v0.y, v1.y);
+        RE[j] = pack2(v0.x, v1.x);
+        IM[j] = pack2(v0.y, v1.y);
       }
     }
     ROpRes cur = s_op[o0];
     for (int k = 0; k < ph.nops; ++k) {
       const ROpRes nxt = s_op[o0 + (k + 1 < ph.nops ? k + 1 : k)];  // prefetch
       if (cur.kind == OP_GATE) {
-        sw2::gate_combo(RE, IM, cur.combo, cur.t, cur.s);
+        gate_combo(RE, IM, cur.combo, cur.t, cur.s);
       } else if (cur.kind == OP_REDUCE) {
         int kr = -1;
 #pragma unroll
@@ -1053,7 +1029,7 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops
         }
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-          const float2 pr = sw2::unpack2(sw2::fma2(RE[j], RE[j], sw2::mul2(IM[j], IM[j])));
+          const float2 pr = unpack2(fma2(RE[j], RE[j], mul2(IM[j], IM[j])));
           if (kr == 0) {
             dn += pr.x;
             up += pr.y;
@@ -1071,7 +1047,7 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops
           for (int q = 0; q < RB; ++q) ureg[q] = 0.f;
 #pragma unroll
           for (int j = 0; j < NP; ++j) {
-            const float2 pr = sw2::unpack2(sw2::fma2(RE[j], RE[j], sw2::mul2(IM[j], IM[j])));
+            const float2 pr = unpack2(fma2(RE[j], RE[j], mul2(IM[j], IM[j])));
             const float sj = pr.x + pr.y;
             tsum += sj;
             ureg[0] += pr.y;
@@ -1107,62 +1083,115 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops
           for (int k = 0; k < RB - 1; ++k)
             if ((j >> k) & 1) o ^= mb[1 + k];
         } else {
-          o ^= mb[1 + sw2::ctz5(g)];
+          o ^= mb[1 + ctz5(g)];
         }
         const uint32_t o1 = o ^ mb[0];
-        const float2 r = sw2::unpack2(RE[j]), i = sw2::unpack2(IM[j]);
+        const float2 r = unpack2(RE[j]), i = unpack2(IM[j]);
         *reinterpret_cast<float2 *>(tw + o) = make_float2(r.x, i.x);
         *reinterpret_cast<float2 *>(tw + o1) = make_float2(r.y, i.y);
       }
     }
-    __syncthreads();
+    sync();
   }
+}
 
-  // ---- shared -> global, output tile bits relabelled by perm.  Output chunk
-  // ch = tid + nt * e of two amplitudes covers output tile index 2 ch: bits
-  // 1..lognt from tid, the RB - 1 high ones from e (Gray order again).  The
-  // amplitude there is input tile index sum of bits perm[q], so its slot is an
-  // XOR of per-bit slots; the chunk's second amplitude is output bit 0 = input
-  // bit perm[0].
-  {
-    uint64_t off_lo = 0;
-    uint32_t pin_lo = 0;
-    for (int k = 0; k < lognt; ++k)
-      if ((tid >> k) & 1) {
-        const int q = d.store_bit[k];
-        off_lo |= 1ull << d.tile_pos[q], pin_lo |= 1u << d.perm[q];
-      }
-    int64_t dh[RB - 1];
-    uint32_t dsl[RB - 1];
-#pragma unroll
-    for (int k = 0; k < RB - 1; ++k) {
-      const int q = d.store_bit[lognt + k];
-      dh[k] = (int64_t)8 << d.tile_pos[q];
-      dsl[k] = sw2::slot(1u << d.perm[q]) << 3;
+// Shared -> global store of a tile, output tile bits relabelled by perm.
+// Output chunk ch = tid + nt * e of two amplitudes covers output tile index
+// 2 ch: bits 1..lognt from tid, the RB - 1 high ones from e (Gray order
+// again).  The amplitude there is input tile index sum of bits perm[q], so its
+// slot is an XOR of per-bit slots; the chunk's second amplitude is output bit
+// 0 = input bit perm[0].
+template <int RB>
+__device__ __forceinline__ void store_tile(float2 *psi, uint64_t base, const PassDesc &d, int tid, int lognt,
+                                           const float2 *tile2) {
+  constexpr int NP = 1 << (RB - 1);
+  uint64_t off_lo = 0;
+  uint32_t pin_lo = 0;
+  for (int k = 0; k < lognt; ++k)
+    if ((tid >> k) & 1) {
+      const int q = d.store_bit[k];
+      off_lo |= 1ull << d.tile_pos[q], pin_lo |= 1u << d.perm[q];
     }
-    const char *tb = reinterpret_cast<const char *>(tile2);
-    const uint32_t sl1 = sw2::slot(1u << d.perm[0]) << 3;
-    const uint32_t so0 = sw2::slot(pin_lo) << 3;
-    char *const dst0 = reinterpret_cast<char *>(psi + base + off_lo);
-    uint32_t so = so0;
-    char *dst = dst0;
+  int64_t dh[RB - 1];
+  uint32_t dsl[RB - 1];
 #pragma unroll
-    for (int g = 0; g < NP; ++g) {
-      if ((g & 7) == 0) {
-        so = so0, dst = dst0;
-#pragma unroll
-        for (int k = 0; k < RB - 1; ++k)
-          if (((g ^ (g >> 1)) >> k) & 1) dst += dh[k], so ^= dsl[k];
-      } else {
-        const int k = sw2::ctz5(g);
-        dst += sw2::gray_up(g) ? dh[k] : -dh[k];
-        so ^= dsl[k];
-      }
-      const float2 v0 = *reinterpret_cast<const float2 *>(tb + so);
-      const float2 v1 = *reinterpret_cast<const float2 *>(tb + (so ^ sl1));
-      *reinterpret_cast<float4 *>(dst) = make_float4(v0.x, v0.y, v1.x, v1.y);
-    }
+  for (int k = 0; k < RB - 1; ++k) {
+    const int q = d.store_bit[lognt + k];
+    dh[k] = (int64_t)8 << d.tile_pos[q];
+    dsl[k] = slot(1u << d.perm[q]) << 3;
   }
+  const char *tb = reinterpret_cast<const char *>(tile2);
+  const uint32_t sl1 = slot(1u << d.perm[0]) << 3;
+  const uint32_t so0 = slot(pin_lo) << 3;
+  char *const dst0 = reinterpret_cast<char *>(psi + base + off_lo);
+  uint32_t so = so0;
+  char *dst = dst0;
+#pragma unroll
+  for (int g = 0; g < NP; ++g) {
+    if ((g & 7) == 0) {
+      so = so0, dst = dst0;
+#pragma unroll
+      for (int k = 0; k < RB - 1; ++k)
+        if (((g ^ (g >> 1)) >> k) & 1) dst += dh[k], so ^= dsl[k];
+    } else {
+      const int k = ctz5(g);
+      dst += gray_up(g) ? dh[k] : -dh[k];
+      so ^= dsl[k];
+    }
+    const float2 v0 = *reinterpret_cast<const float2 *>(tb + so);
+    const float2 v1 = *reinterpret_cast<const float2 *>(tb + (so ^ sl1));
+    *reinterpret_cast<float4 *>(dst) = make_float4(v0.x, v0.y, v1.x, v1.y);
+  }
+}
+
+}  // namespace sw2
+
+// Register-blocked sweep with RB register bits (2^RB amplitudes per thread,
+// 2^(K-RB) threads per tile), one tile per block.
+template <int RB, bool SITES>
+__global__ void __launch_bounds__(RB == 5 ? 512 : 256)
+sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops1,
+              const __grid_constant__ PassDesc d, const PhaseDesc *__restrict__ phases, int M,
+              unsigned ahead) {
+  // one job (gridDim.y == 1): its amplitude and op arrays come with the launch
+  // so the tile copies can start at once; the rest of the job's pointers
+  // (and everything for a batch) from the job table
+  const bool one = gridDim.y == 1;
+  const JobPtrs jp = jobs[blockIdx.y];
+  float2 *__restrict__ psi = one ? psi1 : static_cast<float2 *>(jp.psi);
+  extern __shared__ __align__(16) float2 tile2[];
+  __shared__ uint64_t sH[kMaxK];
+  __shared__ uint64_t sQ[kMaxK * kMaxK];
+  __shared__ uint64_t sOut;
+  __shared__ __align__(16) PhaseDesc s_ph[kMaxPassPhases];
+  __shared__ __align__(16) ROpRes s_op[kMaxPassOps];
+  __shared__ double s_w[SITES ? kMaxWarps * kSiteSlots : 1];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lognt = d.K - RB;
+  const uint64_t base = sw2::tile_origin(blockIdx.x, d, M);
+  // the tile's copies first, then the pass's program (coefficients already
+  // resolved for this dt), then the L2 prefetch of the tile of block
+  // blockIdx.x + ahead (ahead = blocks resident at once): DRAM keeps
+  // streaming while tiles compute, and that block's copies find its tile in L2
+  sw2::load_tile<RB>(psi, base, d, tid, lognt, (uint32_t)__cvta_generic_to_shared(tile2));
+  {
+    const uint32_t *pw = reinterpret_cast<const uint32_t *>(phases + d.phase0);
+    const uint32_t a_ph = (uint32_t)__cvta_generic_to_shared(s_ph);
+    const int nw = d.nphases * (int)(sizeof(PhaseDesc) / 4);
+    for (int i = tid; i < nw; i += nt) sw2::cp_async4(a_ph + 4u * i, pw + i);
+    const ROpRes *so = (one ? sops1 : jp.sops) + d.rop0;
+    const uint32_t a_op = (uint32_t)__cvta_generic_to_shared(s_op);
+    for (int i = tid; i < d.nrops; i += nt) sw2::cp_async16(a_op + 16u * i, so + i);
+  }
+  if (ahead && blockIdx.x + ahead < gridDim.x)
+    sw2::prefetch_tile<RB>(psi, sw2::tile_origin(blockIdx.x + ahead, d, M), d, tid, lognt);
+  sw2::cp_async_wait_all();
+  __syncthreads();
+
+  float up = 0.f, dn = 0.f;
+  sw2::run_phases<RB, SITES>(tile2, d, s_ph, s_op, base, tid, lognt, M, jp.qdiag, up, dn, sH, sQ, &sOut, s_w,
+                             sw2::SyncBlock{});
+  sw2::store_tile<RB>(psi, base, d, tid, lognt, tile2);
   if constexpr (SITES)
     if (d.has_reduce) write_site_partials(d, M, base, s_w, jp.psites);
   if (d.has_reduce) reduce_finalize((double)up, (double)dn, jp, false);

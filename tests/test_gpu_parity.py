@@ -141,6 +141,32 @@ def test_register_blocked_sweeps(kind, rb, K):
     assert np.max(np.abs(amp - psi_w)) <= 2e-6 * 2.0 ** (-(st.M - 1) / 2) * 64
 
 
+@pytest.mark.parametrize("K", [10, 11, 12, 13])
+@pytest.mark.parametrize("kind", ["star16", "ladder16", "generic15", "chain18"])
+def test_register_blocked_sweeps_c128(kind, K):
+    """complex128 tiles of K >= 10 spins run the FP64 register-blocked sweep
+    (five register bits, 16-byte slots): the FP64 bar on P and on every
+    amplitude, over several tiles, segments and relabelling sweeps."""
+    rng = np.random.default_rng(4)
+    a = None
+    if kind == "star16":
+        J, ht = W.star_dipolar(16, 8), spinrp.DIPOLAR
+    elif kind == "ladder16":
+        J, ht = W.ladder(8, 1.0, 0.5), spinrp.XY
+    elif kind == "chain18":
+        J, ht = W.chain(18, 0.9), spinrp.XY
+    else:
+        a = rng.normal(size=(15, 15)); a = a + a.T
+        J, ht = W.star_gaussian(15, 3), spinrp.GENERIC
+    seed, dt, steps = 11, 0.04, 5
+    Pw, Nw, psi_w = _oracle(J, ht, seed, dt, steps, a)
+    Pg, Ng, st = _gpu(J, ht, seed, dt, steps, "c128", a, K=K)
+    assert st.system.plan_info("c128")["K"] == K
+    assert np.max(np.abs(Pg - Pw)) <= TOL_P["c128"]
+    assert np.max(np.abs(Ng - Nw)) <= 1e-12
+    assert np.max(np.abs(st.amplitudes() - psi_w)) <= 1e-12
+
+
 @pytest.mark.parametrize("steps", [1, 2, 3])
 def test_few_steps_and_chunked_evolve(steps):
     J = W.star_dipolar(10, 4)
