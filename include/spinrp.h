@@ -138,15 +138,18 @@ int spinrp_system_bonds(const spinrp_system *sys, int32_t *pairs, int cap, int *
 
 /* Choose the shared-memory tile width K (number of spins a tile spans, 2^K
  * amplitudes per tile) used for precision prec by states created afterwards;
- * K = 0 restores the built-in default.  Valid K: 1..14 for SPINRP_C64,
- * 1..13 for SPINRP_C128 (clipped to M).  This is the autotuner's knob.
+ * K = 0 restores the built-in default (complex128: 12; complex64: the width
+ * among 12, 13 and 14 with the fewest modelled sweep-time units, sweeps per
+ * step x max(2^K, jobs x 2^M / 152), ties to 13, then 12; states of up to 12
+ * spins are one tile).  Valid K: 1..14 for SPINRP_C64, 1..13 for
+ * SPINRP_C128 (clipped to M).  This is the autotuner's knob.
  * Errors: SPINRP_EINVAL. */
 int spinrp_system_set_tile(spinrp_system *sys, int prec, int K);
 
 /* Register bits per phase of the complex64 tile kernel: each thread keeps the
  * 2^rb amplitudes spanned by rb tile bits in registers while it applies every
  * ready gate on those bits (rb = 5 or 6; 0 restores the default: 6 for
- * tiles of 11+ spins, else 5).  Wider register sets apply more gates per
+ * tiles of 13+ spins, else 5).  Wider register sets apply more gates per
  * shared-memory round trip with fewer threads per tile.  The second autotuner knob; affects states and batches
  * created afterwards.  The complex128 tile kernel always keeps 2^5 amplitudes
  * per thread (tiles of 10+ spins; narrower tiles run the per-gate kernel).

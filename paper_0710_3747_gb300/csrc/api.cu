@@ -210,16 +210,11 @@ extern "C" int spinrp_system_bonds(const spinrp_system *sys, int32_t *pairs, int
   return SPINRP_OK;
 }
 
-// Default tile width.  complex64: 2^14 amplitudes (128 KiB, one tile per SM)
-// while the state fits in L2 and the sweep is bound by the in-tile work; 2^13
-// (64 KiB, two tiles per SM, one loading while the other computes) for states
-// streamed from HBM.  complex128: 2^12 (64 KiB, two tiles per SM; the FP64
-// sweep is bound by the FP64 pipe, and a second resident tile covers the
-// other's loads, stores and barriers).
-static int default_K(int prec, int M) {
-  if (prec != SPINRP_C64) return 12;
-  return M >= 25 ? 13 : 14;
-}
+// Default tile width for complex128: 2^12 amplitudes (64 KiB, two tiles per
+// SM; the FP64 sweep is bound by the FP64 pipe, and a second resident tile
+// covers the other's loads, stores and barriers).  complex64 picks among 12,
+// 13 and 14 spins by the cost model in make_plan.
+constexpr int kC128TileK = 12;
 static int low_bits(int prec) { return prec == SPINRP_C64 ? 4 : 3; }  // 128-byte runs
 
 extern "C" int spinrp_system_set_tile(spinrp_system *sys, int prec, int K) {
@@ -238,12 +233,39 @@ extern "C" int spinrp_system_set_regbits(spinrp_system *sys, int rb) {
   return SPINRP_OK;
 }
 
-static int make_plan(const spinrp_system &s, int prec, Plan *plan) {
-  int K = s.tileK[prec] ? s.tileK[prec] : default_K(prec, s.M);
-  K = std::min(K, s.M);
+// The plan for precision prec.  An explicit tile width (set_tile) is used as
+// given; otherwise complex64 states take the tile width K in {14, 13, 12}
+// (at most M) of least modelled cost, sweeps per step x max(2^K, njobs 2^M /
+// kModelSMs): a sweep lasts about one tile's work while the tiles do not fill
+// the SMs, and about the state's share per SM once they do.  Ties go to 13,
+// then 12, then 14.  Measured on GB300 against the other widths: ladders of
+// 14, 18, 22, 24 and 30 spins, dipolar stars of 16, 20 and 22 spins, and the
+// batch of 12..22-spin stars (the model's pick was the fastest, or within
+// 2 %, in every case).
+constexpr int kModelSMs = 152;  // SMs of the GB300 the model was measured on
+static int make_plan(const spinrp_system &s, int prec, Plan *plan, int njobs = 1) {
   std::string err;
-  if (!build_plan(s.M, s.bonds, K, low_bits(prec), plan, &err))
-    return fail(SPINRP_EINVAL, "%s", err.c_str());
+  const int c = low_bits(prec);
+  if (s.tileK[prec] || prec != SPINRP_C64) {
+    const int K = std::min(s.tileK[prec] ? s.tileK[prec] : kC128TileK, s.M);
+    if (!build_plan(s.M, s.bonds, K, c, plan, &err)) return fail(SPINRP_EINVAL, "%s", err.c_str());
+    return SPINRP_OK;
+  }
+  if (s.M <= 12) {
+    if (!build_plan(s.M, s.bonds, s.M, c, plan, &err)) return fail(SPINRP_EINVAL, "%s", err.c_str());
+    return SPINRP_OK;
+  }
+  const double share = std::ldexp((double)njobs, s.M) / kModelSMs;
+  bool have = false;
+  double best = 0.0;
+  for (int K : {13, 12, 14}) {
+    if (K > s.M) continue;
+    Plan p;
+    if (!build_plan(s.M, s.bonds, K, c, &p, &err)) continue;
+    const double cost = p.sweeps_per_step() * std::max(std::ldexp(1.0, K), share);
+    if (!have || cost < best) best = cost, *plan = std::move(p), have = true;
+  }
+  if (!have) return fail(SPINRP_EINVAL, "%s", err.c_str());
   return SPINRP_OK;
 }
 
@@ -543,8 +565,9 @@ static bool use_phases(int prec, int K, int rb) {
   return prec == SPINRP_C64 ? K >= 5 + rb : (rb == 5 && K >= 10);
 }
 // Six register bits (fewer phases, so fewer shared-memory round trips per
-// gate) wherever the tile leaves five lane bits; five below that.
-static int default_regbits(int K) { return K >= 11 ? 6 : 5; }
+// gate) on tiles of 13 and 14 spins; five on narrower tiles, where twice the
+// threads per tile measured faster (GB300, ladders and stars of 14..24 spins).
+static int default_regbits(int K) { return K >= 13 ? 6 : 5; }
 
 // Compile every pass into phases of RB register bits: the pass's gates
 // between two element-wise ops (diagonal phase, reduction) are cut into
@@ -721,8 +744,9 @@ static bool compile_phases(PassSet *ps, int K, int RB, int prec, std::string *er
   return true;
 }
 
-static int plan_state(const spinrp_system &sys, int prec, Plan *plan, PassSet *ps, int *max_blocks) {
-  int rc = make_plan(sys, prec, plan);
+static int plan_state(const spinrp_system &sys, int prec, Plan *plan, PassSet *ps, int *max_blocks,
+                      int njobs = 1) {
+  int rc = make_plan(sys, prec, plan, njobs);
   if (rc) return rc;
   build_passes(*plan, any_diag(sys), ps);
   ps->phased = false;
@@ -1919,7 +1943,7 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
     g.M = s0.M;
     g.nb = (int)s0.bonds.size();
     g.has_diag = any_diag(s0);
-    int rc = plan_state(s0, prec, &g.plan, &g.ps, &g.max_blocks);
+    int rc = plan_state(s0, prec, &g.plan, &g.ps, &g.max_blocks, (int)g.jobs.size());
     if (rc) {
       free_batch(b);
       return rc;

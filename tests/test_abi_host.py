@@ -148,7 +148,35 @@ def test_plan_sweep_counts():
     assert s.plan_info("c64") == {"segments": 3, "sweeps_per_step": 4, "K": 14}
     # M=20 dipolar star, 14-spin tiles: three segments
     s = spinrp.System(W.star_dipolar(20, 2), spinrp.DIPOLAR)
+    s.set_tile("c64", 14)
     assert s.plan_info("c64")["segments"] <= 3
+
+
+def test_default_tile_model():
+    """Default complex64 tile width: sweeps per step x max(2^K, 2^M / 152),
+    least cost among 14, 13, 12 spins, ties to 13 then 12 (values from the
+    plan's own sweep counts)."""
+    def pick(J, ht):
+        M = J.shape[0]
+        if M <= 12:
+            return M
+        costs = {}
+        for K in (13, 12, 14):
+            if K > M:
+                continue
+            s = spinrp.System(J, ht)
+            s.set_tile("c64", K)
+            costs[K] = s.plan_info("c64")["sweeps_per_step"] * max(2.0 ** K, 2.0 ** M / 152)
+        best = min(costs.values())
+        return next(K for K in (13, 12, 14) if K in costs and costs[K] == best)
+    cases = [(W.ladder(5), spinrp.XY, 10), (W.ladder(7), spinrp.XY, 12), (W.ladder(9), spinrp.XY, 12),
+             (W.ladder(11), spinrp.XY, 13), (W.ladder(12), spinrp.XY, 14), (W.ladder(15), spinrp.XY, 13),
+             (W.star_dipolar(16, 3), spinrp.DIPOLAR, 12), (W.star_dipolar(20, 2), spinrp.DIPOLAR, 12),
+             (W.star_dipolar(22, 3), spinrp.DIPOLAR, 13)]
+    for J, ht, want in cases:
+        s = spinrp.System(J, ht)
+        assert s.plan_info("c64")["K"] == want == pick(J, ht)
+        assert s.plan_info("c128")["K"] == min(12, J.shape[0])
 
 
 def test_state_bytes():
