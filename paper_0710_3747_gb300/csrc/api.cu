@@ -8,8 +8,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/spinrp.h"
@@ -310,7 +313,7 @@ struct PassSet {
   // sweep descriptors (host copies) and their op lists
   std::vector<PassDesc> desc;
   std::vector<Op> ops;
-  // register-blocked programs (complex64 path)
+  // register-blocked programs
   std::vector<PhaseDesc> phases;
   std::vector<ROp> rops;
   // launch roles (indices into desc)
@@ -744,8 +747,33 @@ static bool compile_phases(PassSet *ps, int K, int RB, int prec, std::string *er
   return true;
 }
 
-static int plan_state(const spinrp_system &sys, int prec, Plan *plan, PassSet *ps, int *max_blocks,
-                      int njobs = 1) {
+// Plans (sweeps, op lists, register programs) depend only on the bond list,
+// whether any S^zS^z coupling is present, the precision, the tile and
+// register settings and the job count of the tile model; a process-wide cache
+// keyed by those serves repeated systems (serving streams, batches, a
+// footprint query followed by the state it sizes) without re-planning.
+namespace {
+struct PlanKey {
+  int prec, M, tileK, regbits, njobs;
+  bool diag;
+  std::vector<std::pair<int, int>> bonds;
+  bool operator<(const PlanKey &o) const {
+    return std::tie(prec, M, tileK, regbits, njobs, diag, bonds) <
+           std::tie(o.prec, o.M, o.tileK, o.regbits, o.njobs, o.diag, o.bonds);
+  }
+};
+struct PlanEntry {
+  Plan plan;
+  PassSet ps;
+  int max_blocks;
+};
+std::mutex g_plan_mu;
+std::map<PlanKey, PlanEntry> g_plan_cache;
+constexpr size_t kPlanCacheMax = 256;  // entries kept before the cache starts over
+}  // namespace
+
+static int plan_state_uncached(const spinrp_system &sys, int prec, Plan *plan, PassSet *ps,
+                               int *max_blocks, int njobs) {
   int rc = make_plan(sys, prec, plan, njobs);
   if (rc) return rc;
   build_passes(*plan, any_diag(sys), ps);
@@ -770,6 +798,27 @@ static int plan_state(const spinrp_system &sys, int prec, Plan *plan, PassSet *p
     }
   }
   *max_blocks = std::max(init_blocks(sys.M), 1 << (sys.M - plan->K));
+  return SPINRP_OK;
+}
+
+static int plan_state(const spinrp_system &sys, int prec, Plan *plan, PassSet *ps, int *max_blocks,
+                      int njobs = 1) {
+  PlanKey key{prec, sys.M, sys.tileK[prec], sys.regbits, njobs, any_diag(sys), sys.bonds};
+  {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    auto it = g_plan_cache.find(key);
+    if (it != g_plan_cache.end()) {
+      *plan = it->second.plan;
+      *ps = it->second.ps;
+      *max_blocks = it->second.max_blocks;
+      return SPINRP_OK;
+    }
+  }
+  const int rc = plan_state_uncached(sys, prec, plan, ps, max_blocks, njobs);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  if (g_plan_cache.size() >= kPlanCacheMax) g_plan_cache.clear();
+  g_plan_cache.emplace(std::move(key), PlanEntry{*plan, *ps, *max_blocks});
   return SPINRP_OK;
 }
 

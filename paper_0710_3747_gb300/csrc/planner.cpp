@@ -18,6 +18,7 @@
 // On the way back (reverse half step) each sweep undoes its relabelling, so
 // the layout at every step boundary is the same (pos).
 #include <algorithm>
+#include <array>
 #include <limits>
 #include <queue>
 
@@ -236,8 +237,10 @@ bool build_plan(int M, const std::vector<std::pair<int, int>> &bonds, int K, int
 // ---------------------------------------------------------------------------
 namespace {
 
+typedef std::array<uint8_t, kMaxK> BitPtr;  // per tile bit: gates of its chain done
+
 struct PhaseState {
-  std::vector<uint8_t> ptr;  // per bit: gates of its chain done
+  BitPtr ptr;
   int done = 0;
   int pre = 0;               // gates before the fence done
   int parent = -1;           // index into the previous beam level
@@ -247,7 +250,7 @@ struct PhaseState {
 // Apply every gate reachable inside bit set R (smallest index first); gates
 // from `fence` on only once every gate before it is done (*pre counts those).
 int phase_closure(const std::vector<std::pair<int, int>> &g, const std::vector<std::vector<int>> &chain,
-                  std::vector<uint8_t> &ptr, uint32_t R, int fence, int *pre, std::vector<int> *out) {
+                  BitPtr &ptr, uint32_t R, int fence, int *pre, std::vector<int> *out) {
   auto ready = [&](int b) {
     const int u = g[b].first, v = g[b].second;
     return (b < fence || *pre == fence) && ptr[u] < chain[u].size() && chain[u][ptr[u]] == b &&
@@ -292,7 +295,9 @@ bool plan_phases(int K, const std::vector<std::pair<int, int>> &gates, int RB, i
   }
   std::vector<std::vector<PhaseState>> levels(1);
   if (fence < 0 || fence > n) fence = n;
-  levels[0].push_back(PhaseState{std::vector<uint8_t>(K, 0), 0, 0, -1, 0});
+  BitPtr zero;
+  zero.fill(0);
+  levels[0].push_back(PhaseState{zero, 0, 0, -1, 0});
   for (int depth = 0; depth < 4 * n + 4; ++depth) {
     const std::vector<PhaseState> &cur = levels.back();
     std::vector<PhaseState> next;
@@ -348,7 +353,7 @@ bool plan_phases(int K, const std::vector<std::pair<int, int>> &gates, int RB, i
         si = levels[lv][si].parent;
       }
       std::reverse(path.begin(), path.end());
-      std::vector<uint8_t> ptr(K, 0);
+      BitPtr ptr = zero;
       int pre = 0;
       for (uint32_t R : path) {
         std::vector<int> out;

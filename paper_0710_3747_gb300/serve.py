@@ -188,21 +188,23 @@ def main(argv=None):
     ap.add_argument("--chunk", type=int, default=20)
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--prec", default="c64")
+    ap.add_argument("--tile-K", type=int, default=0, help="tile width for every job (0: the library's default)")
     args = ap.parse_args(argv)
+    tile_K = args.tile_K or None
     import torch
     spinrp.lib()
     rate = args.rate
     if rate <= 0:
         probe = W.serve_stream(n=20, seed=args.seed + 1, rate=1e9, m_cap=args.m_cap)
         t = time.perf_counter()
-        run_sequential(probe, args.prec, realtime=False)
+        run_sequential(probe, args.prec, tile_K=tile_K, realtime=False)
         rate = 0.7 * len(probe) / (time.perf_counter() - t)
     jobs = W.serve_stream(n=args.jobs, seed=args.seed, rate=rate, m_cap=args.m_cap)
     t = time.perf_counter()
-    mix = run_stream(jobs, args.prec, max_active=args.max_active, chunk=args.chunk)
+    mix = run_stream(jobs, args.prec, max_active=args.max_active, chunk=args.chunk, tile_K=tile_K)
     wall_mix = time.perf_counter() - t
     t = time.perf_counter()
-    seq = run_sequential(jobs, args.prec)
+    seq = run_sequential(jobs, args.prec, tile_K=tile_K)
     wall_seq = time.perf_counter() - t
     same = max(float(np.max(np.abs(a.P - b.P))) for a, b in zip(mix, seq))
     print(json.dumps({"rate_per_s": rate, "continuous": summary(mix, wall_mix),

@@ -179,6 +179,29 @@ def test_default_tile_model():
         assert s.plan_info("c128")["K"] == min(12, J.shape[0])
 
 
+def test_plan_cache_keys():
+    """Plans are cached by bond list, S^zS^z presence, precision and tile /
+    register settings: systems with equal keys share a plan (schedule and
+    sizes), and every key change gives the plan of its own settings."""
+    a = spinrp.System(W.star_dipolar(16, 3), spinrp.DIPOLAR)
+    b = spinrp.System(W.star_dipolar(16, 4), spinrp.DIPOLAR)  # other couplings, same bonds
+    assert a.schedule() == b.schedule()
+    assert spinrp.state_bytes(a, "c64", 100) == spinrp.state_bytes(b, "c64", 100)
+    assert a.plan_check("c64") == b.plan_check("c64")
+    # the XY form of the same couplings has no S^zS^z term: no diagonal phases
+    c = spinrp.System(W.star_dipolar(16, 3), spinrp.XY)
+    assert c.plan_check("c64")["phases_per_sweep"] < a.plan_check("c64")["phases_per_sweep"]
+    for K in (11, 12, 13, 14):
+        a.set_tile("c64", K)
+        assert a.plan_info("c64")["K"] == K
+        a.plan_check("c64")
+    a.set_regbits(6)
+    a.set_tile("c64", 12)
+    r6 = a.plan_check("c64")
+    a.set_regbits(5)
+    assert a.plan_check("c64") != r6
+
+
 def test_state_bytes():
     s = spinrp.System(W.ladder(7, 1.0, 0.5), spinrp.XY)
     p64, w64 = spinrp.state_bytes(s, "c64", 401)
