@@ -138,7 +138,8 @@ int spinrp_system_bonds(const spinrp_system *sys, int32_t *pairs, int cap, int *
 
 /* Choose the shared-memory tile width K (number of spins a tile spans, 2^K
  * amplitudes per tile) used for precision prec by states created afterwards;
- * K = 0 restores the built-in default (complex128: 12; complex64: the width
+ * K = 0 restores the built-in default (complex128: the widest K <= 12 that
+ * leaves at least 128 tiles, at least 8; complex64: the width
  * among 12, 13 and 14 with the fewest modelled sweep-time units, sweeps per
  * step x max(2^K, jobs x 2^M / 152), ties to 13, then 12; states of up to 12
  * spins are one tile).  Valid K: 1..14 for SPINRP_C64, 1..13 for

@@ -213,11 +213,20 @@ extern "C" int spinrp_system_bonds(const spinrp_system *sys, int32_t *pairs, int
   return SPINRP_OK;
 }
 
-// Default tile width for complex128: 2^12 amplitudes (64 KiB, two tiles per
-// SM; the FP64 sweep is bound by the FP64 pipe, and a second resident tile
-// covers the other's loads, stores and barriers).  complex64 picks among 12,
-// 13 and 14 spins by the cost model in make_plan.
-constexpr int kC128TileK = 12;
+// Default tile width for complex128: the widest K <= 12 that still gives at
+// least 128 tiles (every SM's FP64 pipe busy), at least 8: 12 for states of
+// 19+ spins (64 KiB tiles, two per SM, the register-blocked FP64 sweep at the
+// FP64 pipe's rate), narrower below; 2^8-amplitude tiles (per-gate kernel) for
+// 15 spins and fewer.  Measured on GB300 (us per step, this rule's pick first):
+// 2x6 ladder K8 28.1 against K12 71.5; 14-spin star K8 140.6 against K12
+// 397.2; 2x8 ladder K9 47.5 against K12 98.2 (K8 44.3); 2x9 ladder K11 ~ K12;
+// 20- and 22-spin stars and the 2x15 ladder K12 fastest.  complex64 picks
+// among 12, 13 and 14 spins by the cost model in make_plan.
+static int c128_tile(int M) {
+  for (int K = 12; K >= 8; --K)
+    if (M - K >= 7) return K;
+  return std::min(8, M);
+}
 static int low_bits(int prec) { return prec == SPINRP_C64 ? 4 : 3; }  // 128-byte runs
 
 extern "C" int spinrp_system_set_tile(spinrp_system *sys, int prec, int K) {
@@ -250,7 +259,7 @@ static int make_plan(const spinrp_system &s, int prec, Plan *plan, int njobs = 1
   std::string err;
   const int c = low_bits(prec);
   if (s.tileK[prec] || prec != SPINRP_C64) {
-    const int K = std::min(s.tileK[prec] ? s.tileK[prec] : kC128TileK, s.M);
+    const int K = std::min(s.tileK[prec] ? s.tileK[prec] : c128_tile(s.M), s.M);
     if (!build_plan(s.M, s.bonds, K, c, plan, &err)) return fail(SPINRP_EINVAL, "%s", err.c_str());
     return SPINRP_OK;
   }

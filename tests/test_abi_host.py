@@ -155,7 +155,8 @@ def test_plan_sweep_counts():
 def test_default_tile_model():
     """Default complex64 tile width: sweeps per step x max(2^K, 2^M / 152),
     least cost among 14, 13, 12 spins, ties to 13 then 12 (values from the
-    plan's own sweep counts)."""
+    plan's own sweep counts); complex128: the widest K <= 12 leaving at least
+    128 tiles, at least 8."""
     def pick(J, ht):
         M = J.shape[0]
         if M <= 12:
@@ -176,7 +177,8 @@ def test_default_tile_model():
     for J, ht, want in cases:
         s = spinrp.System(J, ht)
         assert s.plan_info("c64")["K"] == want == pick(J, ht)
-        assert s.plan_info("c128")["K"] == min(12, J.shape[0])
+        M = J.shape[0]
+        assert s.plan_info("c128")["K"] == next((K for K in range(12, 7, -1) if M - K >= 7), min(8, M))
 
 
 def test_plan_cache_keys():
