@@ -254,6 +254,19 @@ int spinrp_site_series(spinrp_state *st, double *out, int64_t cap, int64_t *n);
 /* Same for the norm sum_x |psi_x|^2 after each step. */
 int spinrp_norm_series(spinrp_state *st, double *out, int64_t cap, int64_t *n);
 
+/* Weights of the total-S^z sectors of the current state: out[k] = sum of
+ * |psi_x|^2 over the basis states with k spins up, k = 0..M (the
+ * magnetization distribution; the paper's secular Hamiltonian, section
+ * "Spin systems with different coupling networks", commutes with the total
+ * S^z, so every family conserves it, and the random-phase state of
+ * "Ensemble vs. pure entangled state" starts at out[k] = C(M-1, k-1) /
+ * 2^(M-1)).
+ * FP64 sums in a fixed order (reproducible).  Writes min(cap, M+1) values
+ * and M+1 to *n; reads the whole state once on the state's stream and
+ * synchronizes it.  Errors: SPINRP_EINVAL, SPINRP_ESTATE (not initialized),
+ * SPINRP_ECUDA. */
+int spinrp_sector_norms(spinrp_state *st, double *out, int cap, int *n);
+
 /* Read n amplitudes with LOGICAL basis indices idx[k] (0 <= idx < 2^M) into
  * out (2n doubles, re/im).  Synchronizes. */
 int spinrp_state_read(spinrp_state *st, const int64_t *idx, int64_t n, double *out);

@@ -1476,6 +1476,30 @@ extern "C" int spinrp_norm_series(spinrp_state *st, double *out, int64_t cap, in
   return copy_series(st, 1, out, cap, n);
 }
 
+extern "C" int spinrp_sector_norms(spinrp_state *st, double *out, int cap, int *n) {
+  if (!st || !n || (cap > 0 && !out)) return fail(SPINRP_EINVAL, "sector_norms: bad argument");
+  if (!st->ready) return fail(SPINRP_ESTATE, "sector_norms: state not initialized");
+  const int M = st->M;
+  *n = M + 1;
+  if (cap <= 0) return SPINRP_OK;
+  const int nblk = init_blocks(M);  // <= the state's max_blocks rows of psites
+  double *part = st->psites, *dev_out = reinterpret_cast<double *>(st->stage);
+  g_launches += 2;
+  if (st->prec == SPINRP_C64)
+    sector_kernel<float><<<nblk, 256, 0, st->stream>>>((const float2 *)st->psi, M, part, nblk);
+  else
+    sector_kernel<double><<<nblk, 256, 0, st->stream>>>((const double2 *)st->psi, M, part, nblk);
+  CUDA_TRY(cudaGetLastError());
+  sector_finalize_kernel<<<M + 1, 256, 0, st->stream>>>(part, nblk, dev_out);
+  CUDA_TRY(cudaGetLastError());
+  double buf[kMaxM + 1];
+  CUDA_TRY(cudaMemcpyAsync(buf, dev_out, sizeof(double) * (M + 1), cudaMemcpyDeviceToHost, st->stream));
+  st->d2h += (int64_t)sizeof(double) * (M + 1);
+  CUDA_TRY(cudaStreamSynchronize(st->stream));
+  for (int k = 0; k < std::min(cap, M + 1); ++k) out[k] = buf[k];
+  return SPINRP_OK;
+}
+
 extern "C" int spinrp_profile(spinrp_state *st, int enable) {
   if (!st) return fail(SPINRP_EINVAL, "profile: state is NULL");
   if (enable) {

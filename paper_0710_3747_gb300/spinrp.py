@@ -89,6 +89,7 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             "spinrp_series_length": ([vp], ctypes.c_int64),
             "spinrp_polarization": ([vp, ctypes.c_int, dp, ctypes.c_int64, i64p], ctypes.c_int),
             "spinrp_norm_series": ([vp, dp, ctypes.c_int64, i64p], ctypes.c_int),
+            "spinrp_sector_norms": ([vp, dp, ctypes.c_int, ip], ctypes.c_int),
             "spinrp_state_read": ([vp, i64p, ctypes.c_int64, dp], ctypes.c_int),
             "spinrp_state_layout": ([vp, i32p, ctypes.POINTER(vp)], ctypes.c_int),
             "spinrp_profile": ([vp, ctypes.c_int], ctypes.c_int),
@@ -332,6 +333,13 @@ class State:
         got = ctypes.c_int64()
         _check(lib().spinrp_polarization(self._h, int(site), _dp(out), n, ctypes.byref(got)))
         return out[:got.value]
+
+    def sector_norms(self) -> np.ndarray:
+        """Weights of the total-S^z sectors, k = 0..M spins up (FP64)."""
+        out = np.zeros(self.M + 1)
+        n = ctypes.c_int()
+        _check(lib().spinrp_sector_norms(self._h, _dp(out), self.M + 1, ctypes.byref(n)))
+        return out
 
     def norm_series(self) -> np.ndarray:
         n = self.series_length()
