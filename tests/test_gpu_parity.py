@@ -6,6 +6,7 @@ FP64 path are compared at 1e-11 (a few hundred gate applications of FP64
 rounding); the FP32 initial state at 2e-7 relative (FP32 rounding of the
 phase).
 """
+import math
 import os
 
 import numpy as np
@@ -314,6 +315,10 @@ def test_ladder_m30_sampled():
         assert np.max(np.abs(N - 1.0)) < (1e-10 if prec == "c128" else 1e-5)
         P = st.polarization()
         assert np.all(np.abs(P) <= 1.0 + 1e-6)
+        # total-S^z sector weights: binomial at t = 0, conserved by the flip-flops
+        n = st.sector_norms()
+        want = np.array([0.0] + [math.comb(29, k - 1) / 2.0 ** 29 for k in range(1, 31)])
+        assert np.max(np.abs(n - want)) < (1e-12 if prec == "c128" else 2e-5), prec
         st.close()
 
 
