@@ -1,10 +1,12 @@
 """Batches: many disorder realizations and phase seeds of uneven M evolved
 together (the N_alpha average of the paper's Eq. 4).
 
-Each job of a batch runs the same kernels on the same plan as a single state
-of that system, so its P(t) equals the single-state result bit for bit; a few
-jobs are checked against the FP64 oracle; the device ensemble mean / spread
-equal the host reduction of the per-job series.
+Each job of a batch runs the same kernels as a single state of that system;
+with the same tile width (the default tile model counts a plan group's jobs,
+so large groups may take wider tiles; these small groups do not) it runs the
+same plan, so its P(t) equals the single-state result bit for bit; a few jobs
+are checked against the FP64 oracle; the device ensemble mean / spread equal
+the host reduction of the per-job series.
 """
 import numpy as np
 import pytest
