@@ -284,8 +284,10 @@ int spinrp_state_layout(const spinrp_state *st, int32_t *layout, void **psi);
  * Jobs may differ in M and couplings; jobs with the same sweep plan (same M
  * and bond structure) form a group whose sweeps run as one launch over all
  * its jobs, and the steady-state Trotter steps of all groups are replayed as
- * one CUDA graph.  Device memory (states, tables, series) is allocated by the
- * library with cudaMalloc. */
+ * one CUDA graph.  A group without an explicit tile width takes the default
+ * tile model's width for its job count (see spinrp_system_set_tile), which
+ * for large groups can be wider than a single state's.  Device memory
+ * (states, tables, series) is allocated by the library with cudaMalloc. */
 typedef struct spinrp_batch spinrp_batch;
 
 /* Create a batch of njobs jobs: systems[k] (copied; the caller may destroy it
