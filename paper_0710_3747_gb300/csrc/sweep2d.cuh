@@ -82,14 +82,7 @@ sweep2d_kernel(const JobPtrs *__restrict__ jobs, const __grid_constant__ PassDes
   __shared__ sw2d::SOpD s_op[kMaxPassOps];
   const int K = d.K, tid = threadIdx.x, nt = blockDim.x;
   const int lognt = K - RB;
-  uint64_t base;
-  {
-    const int lane = tid & 31;
-    const uint64_t c = lane < M - K ? (uint64_t)((blockIdx.x >> lane) & 1u) << d.outer_pos[lane] : 0ull;
-    const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)c);
-    const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(c >> 32));
-    base = ((uint64_t)hi << 32) | lo;
-  }
+  const uint64_t base = sw2::tile_origin(blockIdx.x, d, M);
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tile16);
   // ---- global -> shared: 16-byte async copies, amplitude a = tid + nt * e,
   // e in Gray-code order in runs of eight (as in the complex64 kernel)
@@ -139,12 +132,7 @@ sweep2d_kernel(const JobPtrs *__restrict__ jobs, const __grid_constant__ PassDes
   // L2 prefetch of the tile of block blockIdx.x + ahead (128-byte runs: tile
   // bits 0..2, the low physical bits)
   if (ahead && blockIdx.x + ahead < gridDim.x) {
-    const unsigned pb = blockIdx.x + ahead;
-    const int lane = tid & 31;
-    const uint64_t c = lane < M - K ? (uint64_t)((pb >> lane) & 1u) << d.outer_pos[lane] : 0ull;
-    const uint64_t base2 = ((uint64_t)__reduce_or_sync(0xffffffffu, (uint32_t)(c >> 32)) << 32) |
-                           __reduce_or_sync(0xffffffffu, (uint32_t)c);
-    uint64_t ot = base2;
+    uint64_t ot = sw2::tile_origin(blockIdx.x + ahead, d, M);
     for (int b = 0; b < lognt; ++b)
       if ((tid >> b) & 1) ot |= 1ull << d.tile_pos[3 + b];
 #pragma unroll
