@@ -18,6 +18,7 @@
 #include "../../include/spinrp.h"
 #include "internal.h"
 #include "kernels.cuh"
+#include "sectors.cuh"
 #include "sweep2d.cuh"
 
 using namespace spinrp;
