@@ -273,6 +273,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         sysm.set_tile(prec, args.tile_K)
     if args.regbits:
         sysm.set_regbits(args.regbits)
+    tuned = spinrp.autotune(sysm, prec, dt=job.dt) if args.autotune else None
     nb = len(sysm.bonds())
     info = sysm.plan_info(prec)
     st = spinrp.State(sysm, prec, series_cap=job.steps + 1)
@@ -373,6 +374,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "config": {"workload": wname, "M": job.M, "bonds": nb, "trotter_steps": job.steps,
                    "dt": job.dt, "amplitudes": "complex64" if prec == "c64" else "complex128",
                    "tile_K": info["K"], "sweeps_per_step": info["sweeps_per_step"],
+                   "autotuned": None if tuned is None else {"K": tuned["K"], "rb": tuned["rb"]},
                    "state_bytes": amp_bytes * 2 ** job.M,
                    "l2": ("L2 flushed (256 MiB write) before every timed job" if flush is not None
                           else "inputs larger than L2 (state >> 129 MB), no flush"),
@@ -389,6 +391,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 s2.set_tile(prec, args.tile_K)
             if args.regbits:
                 s2.set_regbits(args.regbits)
+            if tuned is not None:
+                s2.set_tile(prec, tuned["K"])
+                if prec == "c64":
+                    s2.set_regbits(tuned["rb"])
             st2 = spinrp.State(s2, prec, series_cap=job.steps + 1)
             st2.init_random_phase(job.seed + rank).evolve(job.dt, job.steps)
             P = st2.polarization()
@@ -470,6 +476,8 @@ def main():
     ap.add_argument("--ref-gates", type=int, default=16)
     ap.add_argument("--tile-K", type=int, default=0, help="tile width override (autotuner knob)")
     ap.add_argument("--regbits", type=int, default=0, help="register bits per phase, 5 or 6 (autotuner knob)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time tile / register-bit candidates first and run the fastest (spinrp.autotune)")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")

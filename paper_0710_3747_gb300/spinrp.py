@@ -408,18 +408,25 @@ def run_job(J, htype: int, seed: int, dt: float, steps: int, prec="c64", a_gener
 
 def autotune(system: System, prec="c64", candidates=None, probe_steps: int = 4, dt: float = 0.02,
              seed: int = 1, repeats: int = 2) -> dict:
-    """Pick the tile width K for `system` by timing `probe_steps` Trotter steps
-    of each candidate on the device (CUDA events, best of `repeats`), then set
-    it with spinrp_system_set_tile.  Returns {"K": best, "ms_per_step": {K: ms}}."""
+    """Pick the tile width K (and, for complex64, the register bits rb) for
+    `system` by timing `probe_steps` Trotter steps of each candidate on the
+    device (CUDA events, best of `repeats`), then set the winner with
+    spinrp_system_set_tile / spinrp_system_set_regbits.  `candidates` is a
+    list of K or of (K, rb) pairs (rb 0 = the library's default for K).
+    Returns {"K": best K, "rb": best rb, "ms_per_step": {(K, rb): ms}}."""
     import torch
     p = _PREC[prec]
     M = system.M
     if candidates is None:
         kmax = 14 if p == C64 else 13
-        candidates = [k for k in range(max(2, min(M, kmax) - 4), min(M, kmax) + 1)]
+        ks = [k for k in range(max(2, min(M, kmax) - 4), min(M, kmax) + 1)]
+        candidates = [(k, rb) for k in ks for rb in ((5, 6) if p == C64 and k >= 11 else (0,))]
+    cands = [c if isinstance(c, tuple) else (int(c), 0) for c in candidates]
     timings = {}
-    for K in candidates:
+    for K, rb in cands:
         system.set_tile(p, K)
+        if p == C64:
+            system.set_regbits(rb)
         st = State(system, p, series_cap=1 + (repeats + 1) * probe_steps)
         st.init_random_phase(seed)
         st.evolve(dt, probe_steps)  # warm-up
@@ -431,11 +438,13 @@ def autotune(system: System, prec="c64", candidates=None, probe_steps: int = 4, 
             e1.record()
             torch.cuda.synchronize()
             best = min(best, e0.elapsed_time(e1) / probe_steps)
-        timings[K] = best
+        timings[(K, rb)] = best
         st.close()
-    K_best = min(timings, key=timings.get)
+    K_best, rb_best = min(timings, key=timings.get)
     system.set_tile(p, K_best)
-    return {"K": K_best, "ms_per_step": timings}
+    if p == C64:
+        system.set_regbits(rb_best)
+    return {"K": K_best, "rb": rb_best, "ms_per_step": timings}
 
 
 # ---------------------------------------------------------------------------

@@ -362,3 +362,22 @@ def test_largest_state_m34():
     assert np.max(np.abs(N - 1.0)) < 1e-5
     assert abs(st.polarization()[-1] - 1.0) < 1e-5
     st.close()
+
+
+def test_autotune_picks_a_measured_candidate():
+    """The autotuner times each (K, rb) candidate, keeps the fastest and sets
+    it on the system; the tuned system still evolves as the oracle does."""
+    J, ht = W.ladder(8, 1.0, 0.5), spinrp.XY
+    s = spinrp.System(J, ht)
+    cands = [(11, 5), (12, 5), (12, 6), (13, 6)]
+    r = spinrp.autotune(s, "c64", candidates=cands, probe_steps=3, dt=0.05)
+    assert set(r["ms_per_step"]) == set(cands)
+    assert (r["K"], r["rb"]) == min(r["ms_per_step"], key=r["ms_per_step"].get)
+    assert s.plan_info("c64")["K"] == r["K"]
+    st = spinrp.State(s, "c64", series_cap=21)
+    st.init_random_phase(3).evolve(0.05, 20)
+    Pw, _, _ = _oracle(J, ht, 3, 0.05, 20)
+    assert np.max(np.abs(st.polarization() - Pw)) <= TOL_P["c64"]
+    st.close()
+    r = spinrp.autotune(s, "c128", candidates=[8, 12], probe_steps=2, dt=0.05)
+    assert r["K"] in (8, 12) and s.plan_info("c128")["K"] == r["K"]
