@@ -204,6 +204,47 @@ def test_plan_cache_keys():
     assert a.plan_check("c64") != r6
 
 
+def test_plan_cache_concurrent_threads():
+    """Plans built and looked up from several host threads at once (the
+    binding releases the GIL during library calls): sparse random graphs whose
+    bond lists no other test uses, so the first lookups race to build; every
+    thread must see the same plans, equal to a serial rebuild of the same
+    systems."""
+    import threading
+    rng = np.random.default_rng(0xCAC4E)
+    systems = []
+    for M in (12, 13, 14, 15, 16, 17):
+        J = rng.normal(size=(M, M)) * (rng.random((M, M)) < 0.3)
+        J = np.triu(J, 1)
+        J = J + J.T
+        J[0, 1] = J[1, 0] = 1.0
+        systems.append((J, spinrp.XY))
+    results = [dict() for _ in range(6)]
+    errors = []
+
+    def worker(k):
+        order = np.random.default_rng(k).permutation(len(systems))
+        try:
+            for i in order:
+                J, ht = systems[i]
+                s = spinrp.System(J, ht)
+                results[k][i] = (spinrp.state_bytes(s, "c64", 50), s.plan_check("c64"),
+                                 spinrp.state_bytes(s, "c128", 50))
+        except Exception as e:  # noqa: BLE001 - reported below
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in range(6)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors[:3]
+    for i, (J, ht) in enumerate(systems):
+        s = spinrp.System(J, ht)
+        want = (spinrp.state_bytes(s, "c64", 50), s.plan_check("c64"), spinrp.state_bytes(s, "c128", 50))
+        assert all(r[i] == want for r in results), i
+
+
 def test_state_bytes():
     s = spinrp.System(W.ladder(7, 1.0, 0.5), spinrp.XY)
     p64, w64 = spinrp.state_bytes(s, "c64", 401)
