@@ -381,3 +381,20 @@ def test_autotune_picks_a_measured_candidate():
     st.close()
     r = spinrp.autotune(s, "c128", candidates=[8, 12], probe_steps=2, dt=0.05)
     assert r["K"] in (8, 12) and s.plan_info("c128")["K"] == r["K"]
+
+
+def test_fp32_error_over_200_steps_m26():
+    """The FP32 path's P(t) against the FP64 path (itself held to 1e-10 of the
+    oracle) over the full 200 steps of the ladder workload's time span, on the
+    2x13 ladder (2^26 amplitudes): the FP32 bar holds with a wide margin."""
+    J = W.ladder(13, 1.0, 0.5)
+    seed, dt, steps = 1, 0.05, 200
+    P = {}
+    for prec in ("c64", "c128"):
+        st = spinrp.State(spinrp.System(J, spinrp.XY), prec, series_cap=steps + 1)
+        st.init_random_phase(seed).evolve(dt, steps)
+        P[prec] = st.polarization()
+        st.close()
+    err = float(np.max(np.abs(P["c64"] - P["c128"])))
+    print(f"max |P_fp32 - P_fp64| over {steps} steps, M = 26: {err:.3e}")
+    assert err <= 1e-5
