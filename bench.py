@@ -277,10 +277,15 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     nb = len(sysm.bonds())
     info = sysm.plan_info(prec)
     st = spinrp.State(sysm, prec, series_cap=job.steps + 1)
+    if args.sites:
+        st.set_sites(True)  # P_{q1}(t) of every spin after every step
     stream = torch.cuda.current_stream()
 
     def one_job():
-        st.init_random_phase(job.seed + rank)
+        if args.product:
+            st.init_product_phase(job.seed + rank)
+        else:
+            st.init_random_phase(job.seed + rank)
         st.evolve(job.dt, job.steps)
 
     for _ in range(args.warmup):
@@ -375,6 +380,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                    "dt": job.dt, "amplitudes": "complex64" if prec == "c64" else "complex128",
                    "tile_K": info["K"], "sweeps_per_step": info["sweeps_per_step"],
                    "autotuned": None if tuned is None else {"K": tuned["K"], "rb": tuned["rb"]},
+                   "all_site_readout": bool(args.sites),
+                   "initial_state": "product" if args.product else "entangled",
                    "state_bytes": amp_bytes * 2 ** job.M,
                    "l2": ("L2 flushed (256 MiB write) before every timed job" if flush is not None
                           else "inputs larger than L2 (state >> 129 MB), no flush"),
@@ -476,6 +483,8 @@ def main():
     ap.add_argument("--ref-gates", type=int, default=16)
     ap.add_argument("--tile-K", type=int, default=0, help="tile width override (autotuner knob)")
     ap.add_argument("--regbits", type=int, default=0, help="register bits per phase, 5 or 6 (autotuner knob)")
+    ap.add_argument("--sites", action="store_true", help="all-site readout P_{q1}(t) of every spin each step")
+    ap.add_argument("--product", action="store_true", help="the paper's product random state instead of the entangled one")
     ap.add_argument("--autotune", action="store_true",
                     help="time tile / register-bit candidates first and run the fastest (spinrp.autotune)")
     ap.add_argument("--skip-e2e", action="store_true")
