@@ -1193,6 +1193,9 @@ static int launch_pass(const LaunchCtx &c, int pass, cudaStream_t stream, bool l
     if (c.prof) prof_mark(c.prof, SPINRP_KERNEL_SWEEP);
     ++g_launches;
   }
+  // the all-site sums are taken only in the sweep that reads P out; the
+  // other sweeps of an all-site run are the plain ones
+  const bool sites = c.sites && c.ps->desc[pass].has_reduce;
   if (sizeof(R) == 4 && c.v2)
   {
     const size_t sm2 = size_t(8) << K;
@@ -1200,24 +1203,24 @@ static int launch_pass(const LaunchCtx &c, int pass, cudaStream_t stream, bool l
     float2 *psi1 = c.njobs == 1 ? static_cast<float2 *>(c.job0.psi) : nullptr;
     const unsigned ahead = c.prefetch_ahead;
     const ROpRes *sops1 = c.njobs == 1 ? c.job0.sops : nullptr;
-    if (c.rb == 6 && c.sites)
+    if (c.rb == 6 && sites)
       sweep2_kernel<6, true><<<grid, 1 << (K - 6), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M,
                                                                         ahead);
     else if (c.rb == 6)
       sweep2_kernel<6, false><<<grid, 1 << (K - 6), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M,
                                                                         ahead);
-    else if (c.sites)
+    else if (sites)
       sweep2_kernel<5, true><<<grid, 1 << (K - 5), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M,
                                                                         ahead);
     else
       sweep2_kernel<5, false><<<grid, 1 << (K - 5), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M,
                                                                         ahead);
   }
-  else if (sizeof(R) == 8 && c.v2 && !c.sites)
-    // complex128 register-blocked (the all-site readout runs the plain kernel)
+  else if (sizeof(R) == 8 && c.v2 && !sites)
+    // complex128 register-blocked (the all-site sums run in the plain kernel)
     sweep2d_kernel<<<grid, 1 << (K - 5), smem, stream>>>(c.jobs, c.ps->desc[pass], c.phases, c.rops, c.M,
                                                           c.prefetch_ahead);
-  else if (c.sites)
+  else if (sites)
     sweep_kernel<R, true><<<grid, nt, smem, stream>>>(c.jobs, c.passes + pass, c.ops, c.M);
   else
     sweep_kernel<R, false><<<grid, nt, smem, stream>>>(c.jobs, c.passes + pass, c.ops, c.M);
