@@ -65,3 +65,26 @@ def test_batch_spread_shrinks_with_m():
         spread[M] = std[10:].mean()
         b.close()
     assert spread[14] < spread[10] / 2.5
+
+
+def test_full_size_batch_sampled_jobs():
+    """The bench's batch at its full size (4096 dipolar stars, M uniform in
+    12..22, the bench's seed and launch configuration) for 5 steps: sampled
+    jobs, including the largest, against the FP64 oracle at the FP32 bar; the
+    device ensemble mean equals the mean of the per-job series."""
+    spinrp.lib()
+    jobs = W.star_batch(n=4096, seed=4, steps=5)
+    systems = [spinrp.System(j.J, j.htype) for j in jobs]
+    b = spinrp.Batch(systems, [j.seed for j in jobs], "c64", series_cap=6)
+    assert b.info()["groups"] == 11
+    b.init_random_phase().evolve(0.02, 5)
+    Ms = np.array([j.M for j in jobs])
+    picks = [0, 1777, 4095, int(np.argmax(Ms)), int(np.argmin(Ms))]
+    for k in picks:
+        j = jobs[k]
+        Pw, _, _ = oracle.run(j.J, j.htype, j.seed, 0.02, 5)
+        assert np.max(np.abs(b.polarization(k) - Pw)) <= 1e-4, (k, j.M)
+    mean, _ = b.ensemble()
+    allP = np.array([b.polarization(k) for k in range(0, 4096, 1)])
+    np.testing.assert_allclose(mean, allP.mean(axis=0), atol=1e-12)
+    b.close()
