@@ -8,6 +8,8 @@ same plan, so its P(t) equals the single-state result bit for bit; a few jobs
 are checked against the FP64 oracle; the device ensemble mean / spread equal
 the host reduction of the per-job series.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -82,9 +84,9 @@ def test_full_size_batch_sampled_jobs():
     picks = [0, 1777, 4095, int(np.argmax(Ms)), int(np.argmin(Ms))]
     for k in picks:
         j = jobs[k]
-        Pw, _, _ = oracle.run(j.J, j.htype, j.seed, 0.02, 5)
+        Pw, _, _ = oracle.run(j.J, j.htype, j.seed, 0.02, 5, threads=os.cpu_count() or 1)
         assert np.max(np.abs(b.polarization(k) - Pw)) <= 1e-4, (k, j.M)
     mean, _ = b.ensemble()
-    allP = np.array([b.polarization(k) for k in range(0, 4096, 1)])
+    allP = np.array([b.polarization(k) for k in range(4096)])
     np.testing.assert_allclose(mean, allP.mean(axis=0), atol=1e-12)
     b.close()
