@@ -406,6 +406,22 @@ def run_job(J, htype: int, seed: int, dt: float, steps: int, prec="c64", a_gener
     return st.polarization(1), st.norm_series(), st
 
 
+def polarized_at(J, m: int, a_generic=None):
+    """Couplings relabelled so that spin m (1-based) becomes spin 1, the spin
+    the random-phase state polarizes: returns (J', a', order) with
+    J'[i, j] = J[order[i], order[j]], order[0] = m - 1 and the other spins in
+    their original order.  A state of the relabelled system gives the paper's
+    W_{m'm} / P_{m'm}(t) (Eq. 2) for a general initially polarized spin m:
+    its spin q is original spin order[q - 1] + 1."""
+    J = np.asarray(J, dtype=np.float64)
+    M = J.shape[0]
+    if not 1 <= m <= M:
+        raise SpinrpError(EINVAL, f"polarized_at: m={m} outside 1..{M}")
+    order = np.array([m - 1] + [q for q in range(M) if q != m - 1])
+    A = None if a_generic is None else np.asarray(a_generic, dtype=np.float64)[np.ix_(order, order)]
+    return J[np.ix_(order, order)], A, order
+
+
 def autotune(system: System, prec="c64", candidates=None, probe_steps: int = 4, dt: float = 0.02,
              seed: int = 1, repeats: int = 2) -> dict:
     """Pick the tile width K (and, for complex64, the register bits rb) for

@@ -103,3 +103,29 @@ def test_sites_off_and_errors():
     with pytest.raises(spinrp.SpinrpError):
         st.polarization(2)
     st.close()
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_general_initial_spin_by_relabelling(prec):
+    """P_{nm}(t) for an initially polarized spin m != 1 (the paper's Eq. 2 in
+    general): relabel spin m to spin 1 (spinrp.polarized_at), read every site
+    out, map back; against the oracle on the relabelled system (same seed,
+    the parity bar) and against exact diagonalization of the original system's
+    2^{-M} Tr[sigma^z_n(t) sigma^z_m] (the random-state scale)."""
+    from oracle import ed
+    spinrp.lib()
+    J, m, dt, steps = W.chain(10, 0.9), 4, 0.05, 60
+    Jp, _, order = spinrp.polarized_at(J, m)
+    assert order[0] == m - 1 and sorted(order) == list(range(10))
+    st = spinrp.State(spinrp.System(Jp, W.XY), prec, series_cap=steps + 1).set_sites(True)
+    st.init_random_phase(9).evolve(dt, steps)
+    got = st.site_series()                                   # columns: relabelled spins
+    P, _, _ = oracle.run_all_sites(Jp, W.XY, 9, dt, steps)
+    assert np.max(np.abs(got - P)) <= (1e-10 if prec == "c128" else 1e-4)
+    a, b = oracle.couplings(J, oracle.XY)
+    times = dt * np.arange(steps + 1)
+    for n in (m, m + 1, 1, 10):
+        ens = ed.ensemble_cross_polarization(a, b, times, n, m=m)
+        col = int(np.flatnonzero(order == n - 1)[0])
+        assert np.max(np.abs(got[:, col] - ens)) < 6 * 2.0 ** (-9 / 2) + 1e-3, n
+    st.close()

@@ -79,3 +79,26 @@ def test_random_state_tracks_free_chain_every_site():
     P, _, _ = oracle.run_all_sites(J, oracle.XY, seed=23, dt=dt, steps=steps, threads=4)
     ff = ed.hopping_pn1(_hopping(J), dt * np.arange(steps + 1))
     assert np.max(np.abs(P - ff)) < 6 * 2.0 ** (-(L - 1) / 2) + 1e-3
+
+
+def test_relabelled_initial_spin_matches_ensemble():
+    """General initially polarized spin m: relabelling m to spin 1
+    (spinrp.polarized_at, pure host arithmetic) and running the oracle's
+    all-site evolution gives P_{nm}(t) of the original system; compared with
+    exact diagonalization of 2^{-M} Tr[sigma^z_n(t) sigma^z_m], averaged over
+    a few seeds so the random-state error (~2^{-(M-1)/2} per seed) shrinks."""
+    from paper_0710_3747_gb300 import spinrp
+    J, m, dt, steps = W.ladder(4, 1.0, 0.6), 6, 0.05, 40
+    M = J.shape[0]
+    Jp, _, order = spinrp.polarized_at(J, m)
+    a, b = oracle.couplings(J, oracle.XY)
+    times = dt * np.arange(steps + 1)
+    runs = [oracle.run_all_sites(Jp, oracle.XY, s, dt, steps)[0] for s in range(1, 9)]
+    mean = np.mean(runs, axis=0)
+    for n in range(1, M + 1):
+        ens = ed.ensemble_cross_polarization(a, b, times, n, m=m)
+        col = int(np.flatnonzero(order == n - 1)[0])
+        assert np.max(np.abs(mean[:, col] - ens)) < 4 * 2.0 ** (-(M - 1) / 2) / np.sqrt(8) + 5e-3, n
+    # and the relabelling is a permutation: the inverse restores J
+    inv = np.argsort(order)
+    np.testing.assert_array_equal(Jp[np.ix_(inv, inv)], J)
