@@ -13,10 +13,14 @@ no flush is needed between steps.
           summed over replicas (N > 1 runs one independent job per GPU);
   e2e     the same through the public API with host inputs and the P(t)
           series copied back (system + state creation, init, evolve, read);
-  roofline  the tile-sweep kernel: algorithmic bytes (one read + one write of
-          the state) per launch / its mean launch time (CUDA events around every
-          launch on the state's stream) against the measured HBM copy peak;
-  fp64    the complex128 path on the same workload (fewer Trotter steps, rate);
+  roofline  the tile-sweep kernel: algorithmic bytes per launch = the
+          minimal-sweep bytes of a Trotter step (two sweeps, each one read and
+          one write of the state) / the plan's sweeps per step, over its mean
+          launch time (CUDA events around every launch on the state's stream),
+          against the measured HBM copy peak; the kernel's own bandwidth (one
+          read and one write of the state per launch) is reported beside it;
+  fp64    the complex128 path on the same workload (all Trotter steps), its
+          rate and the largest FP32-vs-FP64 |dP(t)| over every recorded step;
   cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload.
 
 `--impl reference` times the CPU oracle (there is no other implementation of
@@ -342,11 +346,20 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     upd = updates_per_job(job.M, nb, job.steps)
     value = replica_value(upd, ms / 1e3, world)
 
-    # roofline of the tile-sweep kernel
+    # roofline of the tile-sweep kernel.  Algorithmic bytes are the minimal-sweep
+    # bytes of a Trotter step (2 sweeps, each one read and one write of the
+    # state) shared over the launches of the step: a launch stands for
+    # 1 / sweeps_per_step of a step, so a plan that needs more than 2 sweeps
+    # per step pays for them in this fraction.  The kernel's own bandwidth
+    # (one read and one write of the state per launch) is reported beside it.
     peaks, peak_src = _peaks()
-    bytes_per_launch = 2 * amp_bytes * 2 ** job.M
+    state_bytes = amp_bytes * 2 ** job.M
+    sweep_bytes = 2 * state_bytes
+    min_sweeps = 2 if info["sweeps_per_step"] >= 2 else 1
+    alg_bytes_per_launch = min_sweeps * sweep_bytes / info["sweeps_per_step"]
     sweep_avg_s = sweep_ms / max(sweep_n, 1) / 1e3
-    achieved = bytes_per_launch / sweep_avg_s / 1e9
+    achieved = alg_bytes_per_launch / sweep_avg_s / 1e9
+    kernel_bw = sweep_bytes / sweep_avg_s / 1e9
     traffic = None
     tfile = ROOT / "profiles" / f"traffic_{args.workload}_{prec}.json"
     if tfile.exists():
@@ -363,12 +376,17 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "kernel": ("sweep2_kernel" if info["K"] >= 10 else "sweep_kernel<float>") if prec == "c64"
                 else ("sweep2d_kernel" if info["K"] >= 10 else "sweep_kernel<double>"),
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+                "algorithmic_bytes_per_launch": alg_bytes_per_launch,
+                "algorithmic_bytes": (f"minimal-sweep bytes of a Trotter step ({min_sweeps} sweeps x 2 x "
+                                      f"{amp_bytes} B x 2^{job.M}) / {info['sweeps_per_step']} launches per step"),
+                "frac_of_8TBps": achieved / 8000.0,
                 "launches": sweep_n, "mean_launch_ms": sweep_avg_s * 1e3,
+                "sweep_bandwidth_gbs": kernel_bw, "sweep_bandwidth_frac": kernel_bw / peaks["hbm_gbs"],
                 "sweep_share_of_job": sweep_ms / (ms_prof * args.steps),
                 "timing": "per-launch CUDA events in a second pass over the same jobs (live launches)"}
-    # whole-step roofline: minimal sweeps (2 per step) at the measured peak
-    min_bytes_step = 2 * bytes_per_launch
-    step_roof = {"min_sweeps_per_step": 2, "sweeps_per_step": info["sweeps_per_step"],
+    # the same fraction over whole jobs (graph replays, init included)
+    min_bytes_step = min_sweeps * sweep_bytes
+    step_roof = {"min_sweeps_per_step": min_sweeps, "sweeps_per_step": info["sweeps_per_step"],
                  "frac_of_measured_peak": (min_bytes_step * job.steps / (ms / 1e3) / 1e9) / peaks["hbm_gbs"],
                  "frac_of_8TBps": (min_bytes_step * job.steps / (ms / 1e3) / 1e9) / 8000.0}
 
@@ -421,20 +439,21 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                       "d2h_bytes_per_step": int(d2h), "s_per_step": e2e_s}
 
     # the FP64 (complex128) path on the same workload
-    if not args.skip_fp64 and args.fp64_steps > 0:
-        st64 = spinrp.State(sysm, "c128", series_cap=args.fp64_steps + 1)
+    fp64_steps = job.steps if args.fp64_steps < 0 else args.fp64_steps
+    if not args.skip_fp64 and fp64_steps > 0:
+        st64 = spinrp.State(sysm, "c128", series_cap=fp64_steps + 1)
         st64.init_random_phase(job.seed + rank).evolve(job.dt, 1)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         st64.init_random_phase(job.seed + rank)
         f0.record(stream)
-        st64.evolve(job.dt, args.fp64_steps)
+        st64.evolve(job.dt, fp64_steps)
         f1.record(stream)
         torch.cuda.synchronize()
         ms64 = f0.elapsed_time(f1)
         P64 = st64.polarization()
         n = min(len(P64), len(P32))
-        upd64 = updates_per_job(job.M, nb, args.fp64_steps)
+        upd64 = updates_per_job(job.M, nb, fp64_steps)
         # FP64-pipe roofline: a gate rotates 2^M / 4 flip-flop pairs at 6 FMAs
         # each, 1.5 FMA = 3 FLOP per amplitude update; peak = SMs x max SM
         # clock x 2 FP64 FMA per SM per clock x 2 FLOP
@@ -442,8 +461,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         peak64 = sms * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 * 2 * 2 / 1e12
         ach64 = 3.0 * upd64 / (ms64 / 1e3) / 1e12
         out["fp64"] = {"value": world * upd64 / (ms64 / 1e3),
-                       "unit": UNIT, "trotter_steps": args.fp64_steps, "ms": ms64,
+                       "unit": UNIT, "trotter_steps": fp64_steps, "ms": ms64,
                        "fp32_vs_fp64_max_dP": float(np.max(np.abs(P32[:n] - P64[:n]))),
+                       "fp32_vs_fp64_compared_entries": int(n),
                        "roofline": {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
                                     "frac": ach64 / peak64, "traffic": None,
                                     "kernel": ("sweep2d_kernel" if sysm.plan_info("c128")["K"] >= 10
@@ -478,7 +498,8 @@ def main():
                     choices=["ladder_m30", "star_m20", "ladder_m14", "ladder_m26", "star_batch"])
     ap.add_argument("--batch-jobs", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=500)
-    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--fp64-steps", type=int, default=-1,
+                    help="Trotter steps of the complex128 run (default: all of the workload's)")
     ap.add_argument("--cpu-gates", type=int, default=43)
     ap.add_argument("--ref-gates", type=int, default=16)
     ap.add_argument("--tile-K", type=int, default=0, help="tile width override (autotuner knob)")

@@ -345,7 +345,10 @@ int spinrp_batch_ensemble(spinrp_batch *b, double *mean, double *stddev, int64_t
  *
  * The first call on a device (with that device current) looks up the
  * scratch array's device address; make that first call before any stream
- * capture.  Every call shares the one array and clears its counter itself;
+ * capture.  The address is cached per device with the unique ID of the
+ * context it was looked up in, and looked up again when a call runs in
+ * another context (after the device was reset and its context recreated).
+ * Every call shares the one array and clears its counter itself;
  * calls that overlap on the GPU (different streams, no ordering between them)
  * race on it and must not be issued. */
 int spinrp_polarization_noalloc(const void *psi, int M, int prec, int site, const int32_t *layout,

@@ -86,10 +86,39 @@ noalloc_observe_kernel(const C *__restrict__ psi, int M, int site_pos, NoAllocSc
   }
 }
 
-// Device address of g_noalloc_scratch, looked up once per device.  In host
-// code the array's name is only a host-side stand-in, never a device address.
+// Device address of g_noalloc_scratch.  In host code the array's name is
+// only a host-side stand-in, never a device address, so the address is looked
+// up with cudaGetSymbolAddress on the first call on a device (with that
+// device current) and cached per device together with the unique ID of the
+// context it was resolved in; a call made in a different context (the device
+// was reset and its context recreated) looks it up again.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
 static std::mutex g_noalloc_mu;
 static void *g_noalloc_addr[256];
+static unsigned long long g_noalloc_ctx[256];
+static CtxGetCurrentFn g_ctx_current = nullptr;
+static CtxGetIdFn g_ctx_id = nullptr;
+
+// Unique ID of the calling thread's current context (0 if none can be had).
+static unsigned long long current_context_id() {
+  if (!g_ctx_current || !g_ctx_id) {
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    g_ctx_current = (CtxGetCurrentFn)f1;
+    g_ctx_id = (CtxGetIdFn)f2;
+  }
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_current(&ctx) != 0 || !ctx || g_ctx_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 extern "C" int spinrp_polarization_noalloc(const void *psi, int M, int prec, int site,
                                            const int32_t *layout, int blocks, double *out,
@@ -113,13 +142,17 @@ extern "C" int spinrp_polarization_noalloc(const void *psi, int M, int prec, int
   void *addr = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-      // first call on this device (with it current): resolve the symbol's address
+    const unsigned long long ctx = current_context_id();
+    if (!g_noalloc_addr[dev] || ctx == 0 || ctx != g_noalloc_ctx[dev]) {
+      // first call on this device or in this context (with the device
+      // current): resolve the symbol's address
       if (cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch) != cudaSuccess) {
         g_noalloc_addr[dev] = nullptr;
         cudaGetLastError();
         return report_error(SPINRP_ECUDA, "polarization_noalloc: cudaGetSymbolAddress failed");
       }
+      // the lookup makes the device's context current if it was not yet
+      g_noalloc_ctx[dev] = ctx ? ctx : current_context_id();
     }
     addr = g_noalloc_addr[dev];
   }
