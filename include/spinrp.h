@@ -157,6 +157,22 @@ int spinrp_system_set_tile(spinrp_system *sys, int prec, int K);
  * Errors: SPINRP_EINVAL. */
 int spinrp_system_set_regbits(spinrp_system *sys, int rb);
 
+/* Storage orientation of complex64 states (no counterpart in the paper; a
+ * storage choice of the register-blocked kernel).  When the flip-flop bonds
+ * of the system form a bipartite graph (ladders, chains), its spins are
+ * 2-coloured so that every bond joins the two colours, and a complex64 state
+ * may store each amplitude whose basis index has an odd number of
+ * first-colour spins up with its real and imaginary parts swapped, (Im, Re):
+ * the two amplitudes every gate mixes are then stored in opposite orders and
+ * the gate is applied to the stored words as they are.  mode 1 (default):
+ * states are oriented when the system is bipartite and the register-blocked
+ * program can keep its colour pattern; mode 0: never.  Every readout of the
+ * library (P, norms, spinrp_state_read, sector weights) returns the plain
+ * values; only direct access to the amplitude buffer sees the swap (see
+ * spinrp_state_orientation).  Takes effect for states created afterwards.
+ * Errors: SPINRP_EINVAL. */
+int spinrp_system_set_orientation(spinrp_system *sys, int mode);
+
 /* Describe the sweep plan the library would use for precision prec: number
  * of segments the forward half step is cut into (*segments), device sweeps
  * per Trotter step in the steady state (*sweeps_per_step) and the tile width
@@ -275,6 +291,13 @@ int spinrp_state_read(spinrp_state *st, const int64_t *idx, int64_t n, double *o
  * layout[q] receives the physical bit position of spin q+1 (M ints).  The
  * layout is the same after every complete spinrp_evolve call. */
 int spinrp_state_layout(const spinrp_state *st, int32_t *layout, void **psi);
+
+/* Storage orientation of the state (see spinrp_system_set_orientation):
+ * *black receives the mask of first-colour spins (bit q-1 = spin q) of an
+ * oriented state, whose amplitudes with an odd number of those spins up are
+ * stored (Im, Re) in the buffer spinrp_state_layout reports, or 0 for a
+ * state stored plainly.  Host only. */
+int spinrp_state_orientation(const spinrp_state *st, uint64_t *black);
 
 /* ---- batches of independent jobs ------------------------------------------ */
 

@@ -65,7 +65,41 @@ struct spinrp_system {
   std::vector<std::pair<int, int>> bonds;
   int tileK[2] = {0, 0};
   int regbits = 0;  // register bits per phase of the complex64 kernel (0: default)
+  // 2-colouring of the flip-flop graph (every bond joins the colours), when
+  // one exists: mask of the first-colour spins (see Orientation)
+  bool bipartite = false;
+  uint64_t black = 0;
+  int orient_mode = 1;  // 1: complex64 states are oriented when they can be; 0: never
 };
+
+// Colour the spins of the flip-flop graph with two colours so that every bond
+// joins them (breadth first from each uncoloured spin); false if an odd cycle
+// makes that impossible.  The first colour ("black") is the smaller class.
+static bool two_colour(int M, const std::vector<std::pair<int, int>> &bonds, uint64_t *black) {
+  std::vector<std::vector<int>> adj(M);
+  for (auto &b : bonds) adj[b.first].push_back(b.second), adj[b.second].push_back(b.first);
+  std::vector<int> col(M, -1), queue;
+  for (int r = 0; r < M; ++r) {
+    if (col[r] >= 0) continue;
+    col[r] = 0;
+    queue.assign(1, r);
+    for (size_t h = 0; h < queue.size(); ++h) {
+      const int x = queue[h];
+      for (int y : adj[x]) {
+        if (col[y] < 0) col[y] = 1 - col[x], queue.push_back(y);
+        else if (col[y] == col[x]) return false;
+      }
+    }
+  }
+  int n1 = 0;
+  for (int q = 0; q < M; ++q) n1 += col[q];
+  const int want = 2 * n1 <= M ? 1 : 0;
+  uint64_t m = 0;
+  for (int q = 0; q < M; ++q)
+    if (col[q] == want) m |= 1ull << q;
+  *black = m;
+  return true;
+}
 
 static bool any_diag(const spinrp_system &s) {
   for (int i = 0; i < s.M; ++i)
@@ -112,6 +146,7 @@ extern "C" int spinrp_system_create(int M, const double *J, int htype, const dou
   for (int i = 0; i < M; ++i)
     for (int j = i + 1; j < M; ++j)
       if (s->b[i * M + j] != 0.0) s->bonds.push_back({i, j});
+  s->bipartite = two_colour(M, s->bonds, &s->black);
   *out = s;
   return SPINRP_OK;
 }
@@ -239,6 +274,13 @@ extern "C" int spinrp_system_set_tile(spinrp_system *sys, int prec, int K) {
   return SPINRP_OK;
 }
 
+extern "C" int spinrp_system_set_orientation(spinrp_system *sys, int mode) {
+  if (!sys || (mode != 0 && mode != 1))
+    return fail(SPINRP_EINVAL, "system_set_orientation: mode must be 0 or 1");
+  sys->orient_mode = mode;
+  return SPINRP_OK;
+}
+
 extern "C" int spinrp_system_set_regbits(spinrp_system *sys, int rb) {
   if (!sys || !(rb == 0 || rb == 5 || rb == 6))
     return fail(SPINRP_EINVAL, "system_set_regbits: rb must be 0, 5 or 6");
@@ -332,6 +374,8 @@ struct PassSet {
   int only = -1, first = -1, midstep = -1, last = -1;
   bool phased = false;  // the register-blocked programs are in use
   int rb = 5;           // their register bits per phase
+  bool oriented = false;  // the programs are oriented (and so is the state)
+  uint64_t black = 0;     // first-colour spins (logical mask) when oriented
 };
 
 struct Layout {  // byte offsets inside the work buffer
@@ -380,6 +424,8 @@ struct spinrp_state {
   JobPtrs *d_job = nullptr;   // this state's pointer table (one job)
   JobPtrs hjob{};             // the same, host copy (passed with each sweep launch)
   unsigned prefetch_ahead = 0;  // L2 prefetch distance of the register-blocked sweep
+  uint64_t orient_black = 0;  // oriented state: first-colour spins (logical), else 0
+  uint64_t orient_phys = 0;   // the same as physical positions of the step-boundary layout
   int64_t *d_step = nullptr;  // device series counter
   // CUDA graphs of kGraphSteps steady-state Trotter steps (captured on first use)
   cudaStream_t cap_stream = nullptr;
@@ -589,7 +635,8 @@ static int default_regbits(int K) { return K >= 13 ? 6 : 5; }
 // after the gates it follows.
 constexpr int kPhaseBeam = 8;  // beam width of the phase planner
 
-static bool compile_phases(PassSet *ps, int K, int RB, int prec, std::string *err) {
+static bool compile_phases(PassSet *ps, int M, int K, int RB, int prec, std::string *err,
+                           bool oriented = false, uint64_t black = 0) {
   ps->phases.clear();
   ps->rops.clear();
   const bool wide = prec != SPINRP_C64;  // 16-byte amplitudes, swizzle_slot16
@@ -627,6 +674,15 @@ static bool compile_phases(PassSet *ps, int K, int RB, int prec, std::string *er
     d.phase0 = (int)ps->phases.size();
     d.nphases = 0;
     d.rop0 = (int)ps->rops.size();
+    // oriented: the tile bits and outer positions of first-colour spins
+    d.black_tile = 0;
+    d.black_outer = 0;
+    if (oriented) {
+      for (int q = 0; q < K; ++q)
+        if ((black >> d.tile_spin[q]) & 1ull) d.black_tile |= 1u << q;
+      for (int o = 0; o < M - K; ++o)
+        if ((black >> d.outer_spin[o]) & 1ull) d.black_outer |= 1ull << d.outer_pos[o];
+    }
     std::vector<int> default_rb(RB);
     for (int k = 0; k < RB; ++k) default_rb[k] = k;
     std::vector<ROp> pending;  // element-wise ops waiting for the next phase
@@ -680,35 +736,57 @@ static bool compile_phases(PassSet *ps, int K, int RB, int prec, std::string *er
       std::vector<std::vector<int>> applied;
       const int fz = fence < 0 ? (int)gates.size() : fence;
       int pre_done = 0;
-      if (!plan_phases(K, pairs, RB, kPhaseBeam, fz, &sets, &applied)) {
+      if (!plan_phases(K, pairs, RB, kPhaseBeam, fz, &sets, &applied, d.black_tile,
+                       oriented ? kOrientNbMask(RB) : 0u)) {
         *err = "phase planning failed";
         return false;
       }
       for (size_t k = 0; k < sets.size(); ++k) {
         std::vector<int> rb;
-        for (int q = 0; q < K; ++q)
-          if ((sets[k] >> q) & 1) rb.push_back(q);
-        // register bit 0 is the pack bit of the complex64 kernel: the bit the
-        // fewest of this phase's gates touch (their arithmetic is scalar)
-        int pack = 0, best = 1 << 30;
-        for (int q = 0; q < (int)rb.size(); ++q) {
-          int n = 0;
-          for (int gi : applied[k]) n += (pairs[gi].first == rb[q]) + (pairs[gi].second == rb[q]);
-          if (n < best) best = n, pack = q;
+        if (oriented) {
+          // the NB first-colour bits first, then the others
+          for (int q = 0; q < K; ++q)
+            if (((sets[k] >> q) & 1) && ((d.black_tile >> q) & 1)) rb.push_back(q);
+          for (int q = 0; q < K; ++q)
+            if (((sets[k] >> q) & 1) && !((d.black_tile >> q) & 1)) rb.push_back(q);
+        } else {
+          for (int q = 0; q < K; ++q)
+            if ((sets[k] >> q) & 1) rb.push_back(q);
+          // register bit 0 is the pack bit of the complex64 kernel: the bit the
+          // fewest of this phase's gates touch (their arithmetic is scalar)
+          int pack = 0, best = 1 << 30;
+          for (int q = 0; q < (int)rb.size(); ++q) {
+            int n = 0;
+            for (int gi : applied[k]) n += (pairs[gi].first == rb[q]) + (pairs[gi].second == rb[q]);
+            if (n < best) best = n, pack = q;
+          }
+          std::rotate(rb.begin(), rb.begin() + pack, rb.begin() + pack + 1);
         }
-        std::rotate(rb.begin(), rb.begin() + pack, rb.begin() + pack + 1);
         new_phase(rb);
+        const int nbk = oriented ? __builtin_popcount(sets[k] & d.black_tile) : 0;
+        ps->phases.back().nb = (uint8_t)nbk;
         for (int gi : applied[k]) {
           const PlanGate g{gi, pairs[gi].first, pairs[gi].second};
           int ku = (int)(std::find(rb.begin(), rb.end(), g.i) - rb.begin());
           int kv = (int)(std::find(rb.begin(), rb.end(), g.j) - rb.begin());
           if (ku > kv) std::swap(ku, kv);
-          // combo = index of (ku, kv) among the RB(RB-1)/2 pairs, lexicographic
-          int base_idx = 0;
-          for (int i = 0; i < ku; ++i) base_idx += RB - 1 - i;
+          int combo;
+          if (oriented) {
+            // one bit of each colour: ku < nb <= kv
+            if (!(ku < nbk && kv >= nbk)) {
+              *err = "oriented phase: a gate joins two spins of one colour";
+              return false;
+            }
+            combo = 8 * ku + kv;
+          } else {
+            // combo = index of (ku, kv) among the RB(RB-1)/2 pairs, lexicographic
+            int base_idx = 0;
+            for (int i = 0; i < ku; ++i) base_idx += RB - 1 - i;
+            combo = base_idx + (kv - ku - 1);
+          }
           ROp r{};
           r.kind = OP_GATE;
-          r.combo = (uint8_t)(base_idx + (kv - ku - 1));
+          r.combo = (uint8_t)combo;
           r.coef = gates[g.bond]->coef;
           push_rop(r);
           if (fence >= 0 && gi < fence && ++pre_done == fence) push_rop(fence_op);
@@ -765,11 +843,11 @@ static bool compile_phases(PassSet *ps, int K, int RB, int prec, std::string *er
 namespace {
 struct PlanKey {
   int prec, M, tileK, regbits, njobs;
-  bool diag;
+  bool diag, orient;
   std::vector<std::pair<int, int>> bonds;
   bool operator<(const PlanKey &o) const {
-    return std::tie(prec, M, tileK, regbits, njobs, diag, bonds) <
-           std::tie(o.prec, o.M, o.tileK, o.regbits, o.njobs, o.diag, o.bonds);
+    return std::tie(prec, M, tileK, regbits, njobs, diag, orient, bonds) <
+           std::tie(o.prec, o.M, o.tileK, o.regbits, o.njobs, o.diag, o.orient, o.bonds);
   }
 };
 struct PlanEntry {
@@ -783,16 +861,24 @@ constexpr size_t kPlanCacheMax = 256;  // entries kept before the cache starts o
 }  // namespace
 
 static int plan_state_uncached(const spinrp_system &sys, int prec, Plan *plan, PassSet *ps,
-                               int *max_blocks, int njobs) {
+                               int *max_blocks, int njobs, bool orient) {
   int rc = make_plan(sys, prec, plan, njobs);
   if (rc) return rc;
   build_passes(*plan, any_diag(sys), ps);
   ps->phased = false;
+  ps->oriented = false;
+  ps->black = 0;
   ps->rb = prec != SPINRP_C64 ? 5 : sys.regbits ? sys.regbits : default_regbits(plan->K);
   if (use_phases(prec, plan->K, ps->rb)) {
-    // a program too large to stage in shared memory runs the plain kernel
+    // a program too large to stage in shared memory runs the plain kernel;
+    // complex64 programs of a 2-colourable system are oriented when every
+    // phase can hold its fixed colour pattern, else they are plain
     std::string err;
-    ps->phased = compile_phases(ps, plan->K, ps->rb, prec, &err);
+    if (orient && prec == SPINRP_C64 && sys.bipartite) {
+      ps->oriented = compile_phases(ps, sys.M, plan->K, ps->rb, prec, &err, true, sys.black);
+      if (ps->oriented) ps->black = sys.black;
+    }
+    ps->phased = ps->oriented || compile_phases(ps, sys.M, plan->K, ps->rb, prec, &err);
     if (!ps->phased) ps->phases.clear(), ps->rops.clear();
   }
   // every gate on two distinct bits of its tile; every store permutation a permutation
@@ -812,8 +898,9 @@ static int plan_state_uncached(const spinrp_system &sys, int prec, Plan *plan, P
 }
 
 static int plan_state(const spinrp_system &sys, int prec, Plan *plan, PassSet *ps, int *max_blocks,
-                      int njobs = 1) {
-  PlanKey key{prec, sys.M, sys.tileK[prec], sys.regbits, njobs, any_diag(sys), sys.bonds};
+                      int njobs = 1, bool allow_orient = true) {
+  const bool orient = allow_orient && sys.orient_mode != 0;
+  PlanKey key{prec, sys.M, sys.tileK[prec], sys.regbits, njobs, any_diag(sys), orient, sys.bonds};
   {
     std::lock_guard<std::mutex> lock(g_plan_mu);
     auto it = g_plan_cache.find(key);
@@ -824,7 +911,7 @@ static int plan_state(const spinrp_system &sys, int prec, Plan *plan, PassSet *p
       return SPINRP_OK;
     }
   }
-  const int rc = plan_state_uncached(sys, prec, plan, ps, max_blocks, njobs);
+  const int rc = plan_state_uncached(sys, prec, plan, ps, max_blocks, njobs, orient);
   if (rc) return rc;
   std::lock_guard<std::mutex> lock(g_plan_mu);
   if (g_plan_cache.size() >= kPlanCacheMax) g_plan_cache.clear();
@@ -868,10 +955,15 @@ static int set_smem_limits() {
   CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, wide));
   if (sizeof(R) == 4)
   {
-    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<5, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
-    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
-    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<5, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
-    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<5, false, false>, a, 8 << 14));
+    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6, false, false>, a, 8 << 14));
+    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<5, true, false>, a, 8 << 14));
+    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6, true, false>, a, 8 << 14));
+    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<5, false, true>, a, 8 << 14));
+    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6, false, true>, a, 8 << 14));
+    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<5, true, true>, a, 8 << 14));
+    CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6, true, true>, a, 8 << 14));
   } else {
     CUDA_TRY(cudaFuncSetAttribute(sweep2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 << 13));
   }
@@ -880,7 +972,7 @@ static int set_smem_limits() {
 
 // Register-blocked sweep blocks resident on the whole device at once (the L2
 // prefetch distance); 0 when the query fails.
-static unsigned sweep2_resident(int prec, int rb, int K) {
+static unsigned sweep2_resident(int prec, int rb, int K, bool oriented) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -891,8 +983,14 @@ static unsigned sweep2_resident(int prec, int rb, int K) {
   const cudaError_t e =
       prec != SPINRP_C64
           ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep2d_kernel, 1 << (K - 5), smem)
-      : rb == 6 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep2_kernel<6, false>, 1 << (K - 6), smem)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep2_kernel<5, false>, 1 << (K - 5), smem);
+      : rb == 6 ? (oriented ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep2_kernel<6, false, true>,
+                                                                            1 << (K - 6), smem)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep2_kernel<6, false, false>,
+                                                                            1 << (K - 6), smem))
+                : (oriented ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep2_kernel<5, false, true>,
+                                                                            1 << (K - 5), smem)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep2_kernel<5, false, false>,
+                                                                            1 << (K - 5), smem));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -1011,7 +1109,12 @@ extern "C" int spinrp_state_create(const spinrp_system *sys, int prec, void *str
     free_state(st);
     return rc;
   }
-  if (st->ps.phased) st->prefetch_ahead = sweep2_resident(prec, st->ps.rb, st->plan.K);
+  if (st->ps.phased) st->prefetch_ahead = sweep2_resident(prec, st->ps.rb, st->plan.K, st->ps.oriented);
+  if (st->ps.oriented) {
+    st->orient_black = st->ps.black;
+    for (int q = 0; q < st->M; ++q)
+      if ((st->orient_black >> q) & 1ull) st->orient_phys |= 1ull << st->plan.pos[q];
+  }
   *out = st;
   return SPINRP_OK;
 }
@@ -1062,10 +1165,10 @@ static int state_init(spinrp_state *st, uint64_t seed, int kind) {
   ++g_launches;
   if (st->prec == SPINRP_C64)
     init_kernel<float><<<blocks, 256, 0, st->stream>>>(st->d_job, st->M, layout_arg(st), seed, nullptr,
-                                                       kind);
+                                                       kind, st->orient_black);
   else
     init_kernel<double><<<blocks, 256, 0, st->stream>>>(st->d_job, st->M, layout_arg(st), seed, nullptr,
-                                                        kind);
+                                                        kind, st->orient_black);
   CUDA_TRY(cudaGetLastError());
   int rc = record_sites0(st);
   if (rc) return rc;
@@ -1105,9 +1208,11 @@ extern "C" int spinrp_state_load(spinrp_state *st, const double *amps) {
     ++g_launches;
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
     if (st->prec == SPINRP_C64)
-      scatter_kernel<float><<<blocks, 256, 0, st->stream>>>((float2 *)st->psi, st->stage_idx, n, st->stage);
+      scatter_kernel<float><<<blocks, 256, 0, st->stream>>>((float2 *)st->psi, st->stage_idx, n, st->stage,
+                                                            st->orient_phys);
     else
-      scatter_kernel<double><<<blocks, 256, 0, st->stream>>>((double2 *)st->psi, st->stage_idx, n, st->stage);
+      scatter_kernel<double><<<blocks, 256, 0, st->stream>>>((double2 *)st->psi, st->stage_idx, n, st->stage,
+                                                             st->orient_phys);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(st->stream));
   }
@@ -1143,13 +1248,21 @@ extern "C" int spinrp_state_read(spinrp_state *st, const int64_t *idx, int64_t n
     ++g_launches;
     const int blocks = (int)std::min<int64_t>((m + 255) / 256, 1024);
     if (st->prec == SPINRP_C64)
-      gather_kernel<float><<<blocks, 256, 0, st->stream>>>((const float2 *)st->psi, st->stage_idx, m, st->stage);
+      gather_kernel<float><<<blocks, 256, 0, st->stream>>>((const float2 *)st->psi, st->stage_idx, m, st->stage,
+                                                           st->orient_phys);
     else
-      gather_kernel<double><<<blocks, 256, 0, st->stream>>>((const double2 *)st->psi, st->stage_idx, m, st->stage);
+      gather_kernel<double><<<blocks, 256, 0, st->stream>>>((const double2 *)st->psi, st->stage_idx, m,
+                                                            st->stage, st->orient_phys);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(out + 2 * k0, st->stage, sizeof(double2) * m, cudaMemcpyDeviceToHost, st->stream));
     CUDA_TRY(cudaStreamSynchronize(st->stream));
   }
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_state_orientation(const spinrp_state *st, uint64_t *black) {
+  if (!st || !black) return fail(SPINRP_EINVAL, "state_orientation: bad argument");
+  *black = st->orient_black;
   return SPINRP_OK;
 }
 
@@ -1176,6 +1289,7 @@ struct LaunchCtx {
   JobPtrs job0{};  // host copy of the only job's pointers when njobs == 1
   int njobs = 1;
   int rb = 5;                    // register bits of the register-blocked kernel
+  bool oriented = false;         // oriented program and state (complex64)
   int sites = 0;                 // all-site readout after every reducing sweep
   unsigned prefetch_ahead = 0;   // sweep blocks resident at once (L2 prefetch distance), 0 = off
   spinrp_state *prof = nullptr;  // state whose profiling marks to record, if any
@@ -1203,18 +1317,20 @@ static int launch_pass(const LaunchCtx &c, int pass, cudaStream_t stream, bool l
     float2 *psi1 = c.njobs == 1 ? static_cast<float2 *>(c.job0.psi) : nullptr;
     const unsigned ahead = c.prefetch_ahead;
     const ROpRes *sops1 = c.njobs == 1 ? c.job0.sops : nullptr;
-    if (c.rb == 6 && sites)
-      sweep2_kernel<6, true><<<grid, 1 << (K - 6), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M,
-                                                                        ahead);
-    else if (c.rb == 6)
-      sweep2_kernel<6, false><<<grid, 1 << (K - 6), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M,
-                                                                        ahead);
-    else if (sites)
-      sweep2_kernel<5, true><<<grid, 1 << (K - 5), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M,
-                                                                        ahead);
-    else
-      sweep2_kernel<5, false><<<grid, 1 << (K - 5), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M,
-                                                                        ahead);
+    const int code = (c.rb == 6 ? 4 : 0) | (sites ? 2 : 0) | (c.oriented ? 1 : 0);
+#define SW2(RB_, S_, O_) \
+  sweep2_kernel<RB_, S_, O_><<<grid, 1 << (K - RB_), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M, ahead)
+    switch (code) {
+      case 0: SW2(5, false, false); break;
+      case 1: SW2(5, false, true); break;
+      case 2: SW2(5, true, false); break;
+      case 3: SW2(5, true, true); break;
+      case 4: SW2(6, false, false); break;
+      case 5: SW2(6, false, true); break;
+      case 6: SW2(6, true, false); break;
+      default: SW2(6, true, true); break;
+    }
+#undef SW2
   }
   else if (sizeof(R) == 8 && c.v2 && !sites)
     // complex128 register-blocked (the all-site sums run in the plain kernel)
@@ -1364,6 +1480,7 @@ static LaunchCtx state_ctx(spinrp_state *st) {
   c.K = st->plan.K;
   c.v2 = st->v2;
   c.rb = st->ps.rb;
+  c.oriented = st->ps.oriented;
   c.sites = st->sites ? 1 : 0;
   c.prefetch_ahead = st->prefetch_ahead;
   c.segments = st->plan.segments();
@@ -1574,7 +1691,7 @@ double check_reduce(const std::vector<cplx> &A) {
 uint32_t host_slot(uint32_t t) { return t ^ (((t >> 4) ^ (t >> 8) ^ (t >> 12)) & 15u); }
 
 std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint64_t block, int rb,
-                         size_t nphases_all, size_t nrops_all) {
+                         size_t nphases_all, size_t nrops_all, bool oriented = false) {
   const int K = d.K, nt = 1 << (K - rb), lognt = K - rb;
   if (d.nphases < 0 || d.nphases > kMaxPassPhases || d.nrops < 0 || d.nrops > kMaxPassOps ||
       d.phase0 < 0 || (size_t)d.phase0 + d.nphases > nphases_all || d.rop0 < 0 ||
@@ -1650,9 +1767,30 @@ std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint
           return buf;
         }
       }
-      // the kernel's walk over its packs: byte offsets, runs of eight
+      // the kernel's walk over its packs: byte offsets, runs of eight (an
+      // oriented phase walks all 2^rb words over every register bit)
       const uint32_t ob = s0 << 3;
       uint32_t o = ob;
+      if (oriented) {
+        for (int g = 0; g < (1 << rb); ++g) {
+          const int j = gray(g);
+          if ((g & 7) == 0) {
+            o = ob;
+            for (int k = 0; k < rb; ++k)
+              if ((j >> k) & 1) o ^= (uint32_t)ph.sm[k] << 3;
+          } else {
+            o ^= (uint32_t)ph.sm[low_bit(g)] << 3;
+          }
+          uint32_t s = s0;
+          for (int k = 0; k < rb; ++k)
+            if ((j >> k) & 1) s ^= ph.sm[k];
+          if (o != (s << 3) || (o >> 3) >= T) {
+            snprintf(buf, sizeof buf, "phase %d oriented walk out of place (g=%d)", p, g);
+            return buf;
+          }
+        }
+        continue;
+      }
       for (int g = 0; g < (1 << (rb - 1)); ++g) {
         const int j = gray(g);
         if ((g & 7) == 0) {
@@ -1713,6 +1851,84 @@ std::string audit_sweep2(const PassDesc &d, const PhaseDesc *phases, int M, uint
         snprintf(buf, sizeof buf, "store index out of place (t=%u)", tout);
         return buf;
       }
+    }
+  }
+  return "";
+}
+
+// Host emulation (FP64) of an oriented pass's register arithmetic, thread by
+// thread and word by word as oriented_phase forms it: the stored words
+// (Re, Im) or (Im, Re), the coefficient pairs (t, -t), (-s, s) negated by
+// the parity of the first NB register bits of j and the thread's own
+// orientation; diagonal ops conjugated for odd amplitudes.  Checked against
+// the plain program's result A1 from the same start A0, for both
+// orientations of the tile's outer bits.
+std::string emulate_oriented(const PassDesc &d, const PhaseDesc *phases, const ROp *rops, int rb, int K,
+                             const std::vector<cplx> &A0, const std::vector<cplx> &A1) {
+  const int NA = 1 << rb, lognt = K - rb, nt = 1 << lognt;
+  const size_t T = A0.size();
+  auto par = [](uint64_t x) { return (int)(__builtin_popcountll(x) & 1); };
+  for (int outer = 0; outer < 2; ++outer) {
+    std::vector<double> X(T), Y(T);  // stored words
+    auto ori = [&](size_t t) { return par(t & d.black_tile) ^ outer; };
+    for (size_t t = 0; t < T; ++t) {
+      const bool o = ori(t);
+      X[t] = o ? A0[t].imag() : A0[t].real();
+      Y[t] = o ? A0[t].real() : A0[t].imag();
+    }
+    for (int p = 0; p < d.nphases; ++p) {
+      const PhaseDesc &ph = phases[d.phase0 + p];
+      for (int k = 0; k < ph.nops; ++k) {
+        const ROp &r = rops[ph.op0 + k];
+        if (r.kind == OP_DIAG) {
+          for (size_t t = 0; t < T; ++t) {
+            const double phs = 0.3 * double((t * 2654435761u) % 1000u) / 1000.0 + 0.7 * r.arg;
+            const double c = std::cos(phs), sn = ori(t) ? -std::sin(phs) : std::sin(phs);
+            const double x = X[t], y = Y[t];
+            X[t] = c * x - sn * y, Y[t] = sn * x + c * y;
+          }
+          continue;
+        }
+        if (r.kind != OP_GATE) continue;
+        const int NB = ph.nb, ku = r.combo >> 3, kv = r.combo & 7;
+        if (!((kOrientNbMask(rb) >> NB) & 1u) || ku >= NB || kv < NB || kv >= rb) return "combo out of range";
+        for (int b = 0; b < rb; ++b)
+          if ((int)((d.black_tile >> ph.rb[b]) & 1u) != (b < NB ? 1 : 0)) return "register bits out of colour order";
+        const double th = 0.1 + 0.013 * r.coef, tt = std::tan(0.5 * th), ss = std::sin(th);
+        for (int tid = 0; tid < nt; ++tid) {
+          uint32_t t0 = 0;
+          for (int b = 0; b < 5; ++b) t0 |= ((uint32_t)(tid >> b) & 1u) << ph.lanes[b];
+          for (int b = 0; b < lognt - 5; ++b) t0 |= ((uint32_t)(tid >> (5 + b)) & 1u) << ph.warps[b];
+          const int tp = par(t0 & d.black_tile) ^ outer;
+          auto tix = [&](int j) {
+            uint32_t t = t0;
+            for (int b = 0; b < rb; ++b)
+              if ((j >> b) & 1) t |= 1u << ph.rb[b];
+            return t;
+          };
+          for (int j = 0; j < NA; ++j) {
+            if (!((j >> ku) & 1) || ((j >> kv) & 1)) continue;
+            const int sg = par((uint64_t)j & ((1u << NB) - 1u)) ^ tp;
+            const double T0 = sg ? -tt : tt, T1 = -T0, S0 = sg ? ss : -ss, S1 = -S0;
+            const uint32_t a = tix(j), b = tix(j ^ (1 << ku) ^ (1 << kv));
+            X[a] += T0 * X[b], Y[a] += T1 * Y[b];
+            X[b] += S0 * X[a], Y[b] += S1 * Y[a];
+            X[a] += T0 * X[b], Y[a] += T1 * Y[b];
+          }
+        }
+      }
+    }
+    double err = 0.0, ref = 0.0;
+    for (size_t t = 0; t < T; ++t) {
+      const bool o = ori(t);
+      const cplx v(o ? Y[t] : X[t], o ? X[t] : Y[t]);
+      err = std::max(err, std::abs(v - A1[t]));
+      ref = std::max(ref, std::abs(A1[t]));
+    }
+    if (!(err <= 1e-10 * ref)) {
+      char buf[96];
+      snprintf(buf, sizeof buf, "packed arithmetic differs (%.3e, outer parity %d)", err, outer);
+      return buf;
     }
   }
   return "";
@@ -1869,7 +2085,8 @@ extern "C" int spinrp_system_plan_check(const spinrp_system *sys, int prec, doub
     for (uint64_t blk : {uint64_t(0), nblocks / 3, nblocks - 1}) {
       const std::string e =
           prec == SPINRP_C64
-              ? audit_sweep2(d, ps.phases.data(), plan.M, blk, ps.rb, ps.phases.size(), ps.rops.size())
+              ? audit_sweep2(d, ps.phases.data(), plan.M, blk, ps.rb, ps.phases.size(), ps.rops.size(),
+                             ps.oriented)
               : audit_sweep2d(d, ps.phases.data(), plan.M, blk, ps.phases.size(), ps.rops.size());
       if (!e.empty()) return fail(SPINRP_EINVAL, "plan_check: pass %zu block %llu: %s", pi,
                                   (unsigned long long)blk, e.c_str());
@@ -1877,6 +2094,7 @@ extern "C" int spinrp_system_plan_check(const spinrp_system *sys, int prec, doub
     std::vector<cplx> A(T), B;
     for (auto &x : A) x = cplx(nd(rng), nd(rng));
     B = A;
+    const std::vector<cplx> A0 = A;
     std::vector<double> ra, rb;
     for (int k = 0; k < d.nops; ++k) {
       const Op &op = ps.ops[d.op0 + k];
@@ -1885,8 +2103,12 @@ extern "C" int spinrp_system_plan_check(const spinrp_system *sys, int prec, doub
       else ra.push_back(check_reduce(A));
     }
     std::vector<int> KU, KV;  // combo -> register-bit pair
-    for (int a = 0; a < ps.rb; ++a)
-      for (int bb = a + 1; bb < ps.rb; ++bb) KU.push_back(a), KV.push_back(bb);
+    if (ps.oriented) {
+      for (int c = 0; c < 64; ++c) KU.push_back(c >> 3), KV.push_back(c & 7);
+    } else {
+      for (int a = 0; a < ps.rb; ++a)
+        for (int bb = a + 1; bb < ps.rb; ++bb) KU.push_back(a), KV.push_back(bb);
+    }
     for (int p = 0; p < d.nphases; ++p) {
       const PhaseDesc &ph = ps.phases[d.phase0 + p];
       uint32_t seen = 0;
@@ -1914,6 +2136,10 @@ extern "C" int spinrp_system_plan_check(const spinrp_system *sys, int prec, doub
     double err = 0.0, ref = 0.0;
     for (size_t t = 0; t < T; ++t) err = std::max(err, std::abs(A[t] - B[t])), ref = std::max(ref, std::abs(A[t]));
     if (!(err <= 1e-10 * ref)) return fail(SPINRP_EINVAL, "plan_check: pass %zu differs (%.3e)", pi, err);
+    if (ps.oriented) {
+      const std::string e = emulate_oriented(d, ps.phases.data(), ps.rops.data(), ps.rb, K, A0, A);
+      if (!e.empty()) return fail(SPINRP_EINVAL, "plan_check: pass %zu oriented: %s", pi, e.c_str());
+    }
     if (ra.size() != rb.size()) return fail(SPINRP_EINVAL, "plan_check: pass %zu reductions differ", pi);
     for (size_t k = 0; k < ra.size(); ++k)
       if (std::abs(ra[k] - rb[k]) > 1e-9 * std::abs(ra[k]))
@@ -2029,7 +2255,7 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
     g.M = s0.M;
     g.nb = (int)s0.bonds.size();
     g.has_diag = any_diag(s0);
-    int rc = plan_state(s0, prec, &g.plan, &g.ps, &g.max_blocks, (int)g.jobs.size());
+    int rc = plan_state(s0, prec, &g.plan, &g.ps, &g.max_blocks, (int)g.jobs.size(), false);
     if (rc) {
       free_batch(b);
       return rc;
@@ -2147,7 +2373,7 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
     return rc;
   }
   for (BatchGroup &g : b->groups)
-    if (g.ps.phased) g.ctx.prefetch_ahead = sweep2_resident(prec, g.ps.rb, g.plan.K);
+    if (g.ps.phased) g.ctx.prefetch_ahead = sweep2_resident(prec, g.ps.rb, g.plan.K, false);
   *out = b;
   return SPINRP_OK;
 }
@@ -2178,9 +2404,9 @@ static int batch_init(spinrp_batch *b, int kind) {
     const dim3 grid(init_blocks(g.M), (unsigned)g.jobs.size());
     ++g_launches;
     if (b->prec == SPINRP_C64)
-      init_kernel<float><<<grid, 256, 0, b->stream>>>(g.d_jobs, g.M, group_layout(g), 0, g.d_seeds, kind);
+      init_kernel<float><<<grid, 256, 0, b->stream>>>(g.d_jobs, g.M, group_layout(g), 0, g.d_seeds, kind, 0);
     else
-      init_kernel<double><<<grid, 256, 0, b->stream>>>(g.d_jobs, g.M, group_layout(g), 0, g.d_seeds, kind);
+      init_kernel<double><<<grid, 256, 0, b->stream>>>(g.d_jobs, g.M, group_layout(g), 0, g.d_seeds, kind, 0);
     CUDA_TRY(cudaGetLastError());
   }
   b->len = 1;

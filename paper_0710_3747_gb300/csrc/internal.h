@@ -48,6 +48,10 @@ struct PassDesc {
   int32_t rop0;         //   first op
   int32_t nrops;        //   and number of ops
   uint8_t store_bit[kMaxK];  // store: output tile bit (1..K-1) of each chunk-index bit
+  // oriented states (see Orientation below): tile bits and outer physical
+  // positions that hold spins of the first colour, input layout
+  uint32_t black_tile;
+  uint64_t black_outer;
 };
 
 // Register-blocked execution of a pass.  In a phase every thread holds the
@@ -61,7 +65,7 @@ struct PhaseDesc {
   uint8_t lanes[5];
   uint8_t warps[kMaxK - 10];
   uint8_t nops;
-  uint8_t pad;
+  uint8_t nb;  // oriented program: register bits 0..nb-1 hold first-colour spins
   int32_t op0;
   uint16_t sm[kMaxRegBits];  // shared-memory slot of each register bit
   uint16_t tslot[kMaxK - 5]; // slot of each thread-index bit (lanes, then warps)
@@ -73,6 +77,18 @@ struct PhaseDesc {
 constexpr int kMaxPassPhases = 96;
 constexpr int kMaxPassOps = 768;
 
+// Orientation (complex64 states of a bipartite flip-flop graph).  The spins
+// are 2-coloured so that every bond joins the two colours; an amplitude whose
+// basis index has an odd number of first-colour ("black") spins up is stored
+// with its real and imaginary parts swapped, (Im, Re).  The two amplitudes a
+// gate mixes differ in one black spin, so one is stored (Re, Im) and the
+// other (Im, Re), and the gate's three shears become packed FP32x2 updates
+// of the two stored words as they are (no re/im shuffling).  Each phase of an
+// oriented program holds its nb black register bits first, then the others;
+// nb is one of the counts kOrientNbMask(RB) allows (the kernel has gate code
+// for those).
+inline uint32_t kOrientNbMask(int RB) { return RB == 6 ? 0x1Cu : 0x0Cu; }  // {2,3,4} / {2,3}
+
 // Shared-memory slot of tile index t in the register-blocked kernel: the low
 // four bits are XORed with bits 4-7, 8-11 and 12-15 (XOR-linear).
 inline uint32_t swizzle_slot(uint32_t t) { return t ^ (((t >> 4) ^ (t >> 8) ^ (t >> 12)) & 15u); }
@@ -81,8 +97,8 @@ inline uint32_t swizzle_slot(uint32_t t) { return t ^ (((t >> 4) ^ (t >> 8) ^ (t
 inline uint32_t swizzle_slot16(uint32_t t) { return t ^ (((t >> 3) ^ (t >> 6) ^ (t >> 9) ^ (t >> 12)) & 7u); }
 
 // Op of a phase: GATE acts on register bits given by `combo` (index of the
-// pair (ku < kv) among the RB(RB-1)/2 pairs, lexicographic); DIAG / REDUCE as
-// in Op.
+// pair (ku < kv) among the RB(RB-1)/2 pairs, lexicographic; in an oriented
+// program ku < nb <= kv and combo = 8 ku + kv); DIAG / REDUCE as in Op.
 struct ROp {
   uint8_t kind;
   uint8_t combo;
@@ -162,8 +178,11 @@ bool build_plan(int M, const std::vector<std::pair<int, int>> &bonds, int K, int
 // mask) applies the gates applied[k], in an order that keeps every bit's gate
 // sequence, and no gate from index `fence` on before every gate ahead of it
 // (an element-wise op sits between them).  Beam search of width `beam` for
-// few phases.  False if a gate cannot be placed.
+// few phases.  With nb_allowed != 0 every set holds nb bits of the mask
+// `black` and RB - nb others for an nb whose bit is set in nb_allowed (the
+// oriented kernel's colour patterns).  False if a gate cannot be placed.
 bool plan_phases(int K, const std::vector<std::pair<int, int>> &gates, int RB, int beam, int fence,
-                 std::vector<uint32_t> *sets, std::vector<std::vector<int>> *applied);
+                 std::vector<uint32_t> *sets, std::vector<std::vector<int>> *applied,
+                 uint32_t black = 0, uint32_t nb_allowed = 0);
 
 }  // namespace spinrp

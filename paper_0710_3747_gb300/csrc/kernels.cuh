@@ -255,10 +255,12 @@ sites_finalize_kernel(const JobPtrs *__restrict__ jobs, int M, int nblk) {
 // fixed-point turns.
 enum InitKind { INIT_ENTANGLED = 0, INIT_PRODUCT = 1 };
 
+// orient: logical mask of the first-colour spins of an oriented state (0 for
+// a plain one): amplitudes with an odd number of them up are stored (Im, Re).
 template <typename R>
 __global__ void __launch_bounds__(256)
 init_kernel(const JobPtrs *__restrict__ jobs, int M, LayoutArg lay, uint64_t seed0,
-            const uint64_t *__restrict__ seeds, int kind) {
+            const uint64_t *__restrict__ seeds, int kind, uint64_t orient) {
   using C = typename CT<R>::T;
   const JobPtrs jp = jobs[blockIdx.y];
   C *__restrict__ psi = static_cast<C *>(jp.psi);
@@ -311,6 +313,10 @@ init_kernel(const JobPtrs *__restrict__ jobs, int M, LayoutArg lay, uint64_t see
       }
       v.x = amp * e.x, v.y = amp * e.y;
       up += v.x * v.x + v.y * v.y;
+    }
+    if (__popcll(x & orient) & 1) {
+      const R t = v.x;
+      v.x = v.y, v.y = t;
     }
     psi[y] = v;
   }
@@ -565,24 +571,28 @@ sweep_kernel(const JobPtrs *__restrict__ jobs, const PassDesc *__restrict__ pdes
 }
 
 // Gather amplitudes at physical indices into a staging buffer (FP64 pairs).
+// orient: physical positions of the first-colour spins of an oriented state
+// (0 for a plain one); those amplitudes stored (Im, Re) are read back as (Re, Im).
 template <typename R>
 __global__ void gather_kernel(const typename CT<R>::T *__restrict__ psi,
-                              const int64_t *__restrict__ idx, int64_t n, double2 *out) {
+                              const int64_t *__restrict__ idx, int64_t n, double2 *out, uint64_t orient) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const typename CT<R>::T v = psi[idx[k]];
-    out[k] = make_double2((double)v.x, (double)v.y);
+    const bool sw = __popcll((uint64_t)idx[k] & orient) & 1;
+    out[k] = sw ? make_double2((double)v.y, (double)v.x) : make_double2((double)v.x, (double)v.y);
   }
 }
 
 template <typename R>
 __global__ void scatter_kernel(typename CT<R>::T *__restrict__ psi, const int64_t *__restrict__ idx,
-                               int64_t n, const double2 *__restrict__ in) {
+                               int64_t n, const double2 *__restrict__ in, uint64_t orient) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     typename CT<R>::T v;
-    v.x = (R)in[k].x;
-    v.y = (R)in[k].y;
+    const bool sw = __popcll((uint64_t)idx[k] & orient) & 1;
+    v.x = (R)(sw ? in[k].y : in[k].x);
+    v.y = (R)(sw ? in[k].x : in[k].y);
     psi[idx[k]] = v;
   }
 }
@@ -862,18 +872,318 @@ __device__ __forceinline__ void prefetch_tile(const float2 *psi, uint64_t base2,
   }
 }
 
+// Tile index of this thread's subcube origin in phase ph (register bits clear).
+__device__ __forceinline__ uint32_t thread_origin(const PhaseDesc &ph, int tid, int lognt) {
+  uint32_t t0 = 0;
+  for (int k = 0; k < 5; ++k) t0 |= ((uint32_t)(tid >> k) & 1u) << ph.lanes[k];
+  for (int k = 0; k < lognt - 5; ++k) t0 |= ((uint32_t)(tid >> (5 + k)) & 1u) << ph.warps[k];
+  return t0;
+}
+
+// The diagonal phase e^{-i tau D}, amplitude by amplitude in shared memory.
+// ORIENT: amplitudes of odd orientation are stored (Im, Re) and take the
+// conjugate phase (the stored word is i conj(psi), and i conj(psi e^{ia}) =
+// i conj(psi) e^{-ia}).
+template <int RB, bool ORIENT, typename Sync>
+__device__ __forceinline__ void diag_phase(float2 *tile2, const PassDesc &d, const PhaseDesc &ph,
+                                           const ROpRes &op, uint64_t base, int tid, int lognt, int M,
+                                           const uint64_t *__restrict__ qdiag, uint64_t *sH, uint64_t *sQ,
+                                           uint64_t *sOut, uint32_t s0, const uint32_t (&sm)[RB], Sync sync) {
+  constexpr int NA = 1 << RB;
+  const int K = d.K, nt = 1 << lognt;
+  const int nout = M - K;
+  // Theta(x) = sum_{p<p'} q_pp' sigma_p sigma_p' (mod 2^64) split into
+  // outer-outer (sOut), outer-tile (sH) and tile-tile (sQ) parts
+  uint32_t t0 = 0;
+  for (int k = 0; k < 5; ++k) t0 |= ((uint32_t)(tid >> k) & 1u) << ph.lanes[k];
+  for (int k = 0; k < lognt - 5; ++k) t0 |= ((uint32_t)(tid >> (5 + k)) & 1u) << ph.warps[k];
+  const uint64_t *q = qdiag + (size_t)op.arg * M * M;
+  if (tid < K) {
+    const int pp = d.tile_pos[tid];
+    uint64_t h = 0;
+    for (int o = 0; o < nout; ++o) {
+      const int po = d.outer_pos[o];
+      const uint64_t v = q[pp * M + po];
+      h += ((base >> po) & 1ull) ? v : (0ull - v);
+    }
+    sH[tid] = h;
+  } else if (tid == K) {
+    uint64_t s = 0;
+    for (int o = 0; o < nout; ++o)
+      for (int o2 = o + 1; o2 < nout; ++o2) {
+        const int pa = d.outer_pos[o], pb = d.outer_pos[o2];
+        const uint64_t v = q[pa * M + pb];
+        s += (((base >> pa) ^ (base >> pb)) & 1ull) ? (0ull - v) : v;
+      }
+    *sOut = s;
+  }
+  for (int w = tid; w < K * K; w += nt) sQ[w] = q[d.tile_pos[w / K] * M + d.tile_pos[w % K]];
+  sync();
+  uint32_t isreg = 0;
+  for (int k = 0; k < RB; ++k) isreg |= 1u << ph.rb[k];
+  // fixed part (tile bits from the thread index) once per thread
+  uint64_t th0 = *sOut;
+  for (int x = 0; x < K; ++x) {
+    if ((isreg >> x) & 1u) continue;
+    const uint32_t bx = (t0 >> x) & 1u;
+    th0 += bx ? sH[x] : (0ull - sH[x]);
+    for (int y = x + 1; y < K; ++y) {
+      if ((isreg >> y) & 1u) continue;
+      th0 += (bx ^ ((t0 >> y) & 1u)) ? (0ull - sQ[x * K + y]) : sQ[x * K + y];
+    }
+  }
+  // field on each register bit from the fixed bits, once per thread
+  uint64_t G[RB];
+#pragma unroll
+  for (int k = 0; k < RB; ++k) {
+    const int rk = ph.rb[k];
+    uint64_t g = sH[rk];
+    for (int x = 0; x < K; ++x) {
+      if ((isreg >> x) & 1u) continue;
+      g += ((t0 >> x) & 1u) ? sQ[x * K + rk] : (0ull - sQ[x * K + rk]);
+    }
+    G[k] = g;
+  }
+  // the register combinations in Gray-code order: with sigma_k = +1 for a
+  // set bit and -1 for a clear one, Theta = th0 + sum_k sigma_k G_k +
+  // sum_{k<l} sigma_k sigma_l Q_kl; flipping bit k changes Theta by
+  // -2 sigma_k F_k, F_k = G_k + sum_{l!=k} sigma_l Q_kl its field, and
+  // every other field F_l by -2 sigma_k Q_kl (exact, modulo 2^64)
+  uint64_t Qr[RB][RB], F[RB];
+#pragma unroll
+  for (int k = 0; k < RB; ++k)
+#pragma unroll
+    for (int l = 0; l < RB; ++l)
+      Qr[k][l] = k == l ? 0ull : sQ[ph.rb[k < l ? k : l] * K + ph.rb[k < l ? l : k]];
+  uint64_t th = th0;
+#pragma unroll
+  for (int k = 0; k < RB; ++k) {
+    th -= G[k];
+    F[k] = G[k];
+#pragma unroll
+    for (int l = 0; l < RB; ++l) {
+      if (l == k) continue;
+      F[k] -= Qr[k][l];
+      if (l > k) th += Qr[k][l];
+    }
+  }
+  uint32_t s = s0;
+  // orientation of the current amplitude and of each register bit
+  uint32_t ori = 0, obit[RB];
+  if constexpr (ORIENT) {
+    ori = (__popc(t0 & d.black_tile) ^ __popcll(base & d.black_outer)) & 1u;
+#pragma unroll
+    for (int k = 0; k < RB; ++k) obit[k] = (d.black_tile >> ph.rb[k]) & 1u;
+  }
+#pragma unroll
+  for (int g = 0; g < NA; ++g) {
+    if (g) {
+      const int k = ctz6(g);
+      // sigma_k before the flip: +1 when the bit is set in gray(g - 1)
+      const bool was_up = ((((g - 1) ^ ((g - 1) >> 1)) >> k) & 1) != 0;
+      th += was_up ? (0ull - 2ull * F[k]) : 2ull * F[k];
+#pragma unroll
+      for (int l = 0; l < RB; ++l)
+        if (l != k) F[l] += was_up ? (0ull - 2ull * Qr[l][k]) : 2ull * Qr[l][k];
+      s ^= sm[k];
+      if constexpr (ORIENT) ori ^= obit[k];
+    }
+    float2 e = cis_turns(th, 0.0f);
+    if constexpr (ORIENT) e.y = ori ? -e.y : e.y;
+    tile2[s] = cmul(tile2[s], e);
+  }
+  sync();
+}
+
+// Register-blocked phases of an oriented program (see Orientation): the
+// thread's 2^RB amplitudes are NA words P[j], j = register bits (the first NB
+// = ph.nb of them of the first colour), each the stored (Re, Im) or (Im, Re)
+// pair as is.  A gate on register bits (JU < NB <= JV) updates the pairs (j, k = j ^
+// 2^JU ^ 2^JV), j with bit JU set, by P[j] += T P[k]; P[k] += S P[j]; P[j] +=
+// T P[k] (packed FP32x2), with T = (t, -t), S = (-s, s) when amplitude j is
+// stored (Re, Im) and both negated when it is stored (Im, Re): the three
+// shears of shear_rotate, the second plane's written y-first (y -= t x,
+// x += s y, y -= t x, the same rotation).  Orientation of j = parity of its
+// first-colour register bits (compile time) XOR the thread's (folded into T, S).
+// parity of the low nb bits of j (folded to a constant for a constant j)
+__device__ __forceinline__ bool par_low(int j, int nb) { return (__popc((unsigned)j & ((1u << nb) - 1u)) & 1) != 0; }
+
+template <int NA, int NB, int JU, int JV>
+__device__ __forceinline__ void gate_oriented(u64 (&P)[NA], u64 T, u64 S) {
+  constexpr u64 kNeg = 0x8000000080000000ull;
+  const u64 Tn = T ^ kNeg, Sn = S ^ kNeg;
+#pragma unroll
+  for (int j = 0; j < NA; ++j)
+    if (((j >> JU) & 1) == 1 && ((j >> JV) & 1) == 0)
+      fma2_acc(P[j], par_low(j, NB) ? Tn : T, P[j ^ (1 << JU) ^ (1 << JV)]);
+#pragma unroll
+  for (int j = 0; j < NA; ++j)
+    if (((j >> JU) & 1) == 1 && ((j >> JV) & 1) == 0)
+      fma2_acc(P[j ^ (1 << JU) ^ (1 << JV)], par_low(j, NB) ? Sn : S, P[j]);
+#pragma unroll
+  for (int j = 0; j < NA; ++j)
+    if (((j >> JU) & 1) == 1 && ((j >> JV) & 1) == 0)
+      fma2_acc(P[j], par_low(j, NB) ? Tn : T, P[j ^ (1 << JU) ^ (1 << JV)]);
+}
+
+// Gate on register bits (ku, kv) of a phase with nb first-colour register
+// bits: key = 64 nb + 8 ku + kv.
+__device__ __forceinline__ void gate_combo_oriented(u64 (&P)[64], int key, u64 T, u64 S) {
+  switch (key) {
+    case 130: gate_oriented<64, 2, 0, 2>(P, T, S); break;
+    case 131: gate_oriented<64, 2, 0, 3>(P, T, S); break;
+    case 132: gate_oriented<64, 2, 0, 4>(P, T, S); break;
+    case 133: gate_oriented<64, 2, 0, 5>(P, T, S); break;
+    case 138: gate_oriented<64, 2, 1, 2>(P, T, S); break;
+    case 139: gate_oriented<64, 2, 1, 3>(P, T, S); break;
+    case 140: gate_oriented<64, 2, 1, 4>(P, T, S); break;
+    case 141: gate_oriented<64, 2, 1, 5>(P, T, S); break;
+    case 195: gate_oriented<64, 3, 0, 3>(P, T, S); break;
+    case 196: gate_oriented<64, 3, 0, 4>(P, T, S); break;
+    case 197: gate_oriented<64, 3, 0, 5>(P, T, S); break;
+    case 203: gate_oriented<64, 3, 1, 3>(P, T, S); break;
+    case 204: gate_oriented<64, 3, 1, 4>(P, T, S); break;
+    case 205: gate_oriented<64, 3, 1, 5>(P, T, S); break;
+    case 211: gate_oriented<64, 3, 2, 3>(P, T, S); break;
+    case 212: gate_oriented<64, 3, 2, 4>(P, T, S); break;
+    case 213: gate_oriented<64, 3, 2, 5>(P, T, S); break;
+    case 260: gate_oriented<64, 4, 0, 4>(P, T, S); break;
+    case 261: gate_oriented<64, 4, 0, 5>(P, T, S); break;
+    case 268: gate_oriented<64, 4, 1, 4>(P, T, S); break;
+    case 269: gate_oriented<64, 4, 1, 5>(P, T, S); break;
+    case 276: gate_oriented<64, 4, 2, 4>(P, T, S); break;
+    case 277: gate_oriented<64, 4, 2, 5>(P, T, S); break;
+    case 284: gate_oriented<64, 4, 3, 4>(P, T, S); break;
+    case 285: gate_oriented<64, 4, 3, 5>(P, T, S); break;
+    default: break;
+  }
+}
+__device__ __forceinline__ void gate_combo_oriented(u64 (&P)[32], int key, u64 T, u64 S) {
+  switch (key) {
+    case 130: gate_oriented<32, 2, 0, 2>(P, T, S); break;
+    case 131: gate_oriented<32, 2, 0, 3>(P, T, S); break;
+    case 132: gate_oriented<32, 2, 0, 4>(P, T, S); break;
+    case 138: gate_oriented<32, 2, 1, 2>(P, T, S); break;
+    case 139: gate_oriented<32, 2, 1, 3>(P, T, S); break;
+    case 140: gate_oriented<32, 2, 1, 4>(P, T, S); break;
+    case 195: gate_oriented<32, 3, 0, 3>(P, T, S); break;
+    case 196: gate_oriented<32, 3, 0, 4>(P, T, S); break;
+    case 203: gate_oriented<32, 3, 1, 3>(P, T, S); break;
+    case 204: gate_oriented<32, 3, 1, 4>(P, T, S); break;
+    case 211: gate_oriented<32, 3, 2, 3>(P, T, S); break;
+    case 212: gate_oriented<32, 3, 2, 4>(P, T, S); break;
+    default: break;
+  }
+}
+
+template <int RB, bool SITES>
+__device__ __forceinline__ void oriented_phase(float2 *tile2, const PassDesc &d, const PhaseDesc &ph,
+                                               const ROpRes *ops, uint64_t base, int tid, int lognt,
+                                               float &up, float &dn, double *s_w, uint32_t s0,
+                                               const uint32_t (&sm)[RB], uint32_t outer_par) {
+  constexpr int NA = 1 << RB;
+  const uint32_t t0 = thread_origin(ph, tid, lognt);
+  const int key0 = 64 * ph.nb;
+  // the thread's orientation: its fixed tile bits and the tile's outer bits
+  const uint32_t tp = (__popc(t0 & d.black_tile) & 1u) ^ outer_par;
+  const u64 flip = tp ? 0x8000000080000000ull : 0ull;
+  u64 P[NA];
+  const char *tb = reinterpret_cast<const char *>(tile2);
+  uint32_t mb[RB];
+#pragma unroll
+  for (int k = 0; k < RB; ++k) mb[k] = sm[k] << 3;
+  const uint32_t ob = s0 << 3;
+  {
+    uint32_t o = ob;
+#pragma unroll
+    for (int g = 0; g < NA; ++g) {
+      const int j = g ^ (g >> 1);
+      if ((g & 7) == 0) {
+        o = ob;
+#pragma unroll
+        for (int k = 0; k < RB; ++k)
+          if ((j >> k) & 1) o ^= mb[k];
+      } else {
+        o ^= mb[ctz6(g)];
+      }
+      P[j] = *reinterpret_cast<const u64 *>(tb + o);
+    }
+  }
+  ROpRes cur = ops[0];
+  for (int k = 0; k < ph.nops; ++k) {
+    const ROpRes nxt = ops[k + 1 < ph.nops ? k + 1 : k];  // prefetch
+    if (cur.kind == OP_GATE) {
+      const u64 T = pack2(cur.t, -cur.t) ^ flip, S = pack2(-cur.s, cur.s) ^ flip;
+      gate_combo_oriented(P, key0 + cur.combo, T, S);
+    } else if (cur.kind == OP_REDUCE) {
+      int kr = -1;
+#pragma unroll
+      for (int q = 0; q < RB; ++q)
+        if (ph.rb[q] == d.site_tile) kr = q;
+      const uint32_t fixed_bit = d.site_tile < 0 ? (uint32_t)((base >> d.site_pos) & 1ull)
+                                                 : (t0 >> d.site_tile) & 1u;
+      float tsum = 0.f, ureg[RB];
+#pragma unroll
+      for (int q = 0; q < RB; ++q) ureg[q] = 0.f;
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const float2 v = unpack2(P[j]);
+        const float pr = fmaf(v.x, v.x, v.y * v.y);
+        const uint32_t bit = kr >= 0 ? ((uint32_t)(j >> kr) & 1u) : fixed_bit;
+        if (bit) up += pr;
+        else dn += pr;
+        if constexpr (SITES) {
+          tsum += pr;
+#pragma unroll
+          for (int q = 0; q < RB; ++q)
+            if ((j >> q) & 1) ureg[q] += pr;
+        }
+      }
+      if constexpr (SITES) {
+#pragma unroll
+        for (int q = 0; q < kMaxK; ++q) {
+          float v = ((t0 >> q) & 1u) ? tsum : 0.f;
+#pragma unroll
+          for (int k2 = 0; k2 < RB; ++k2)
+            if (ph.rb[k2] == q) v = ureg[k2];
+          warp_site_sum<float>(v, q, s_w);
+        }
+        warp_site_sum<float>(tsum, kMaxK, s_w);
+      }
+    }
+    cur = nxt;
+  }
+  {
+    char *tw = reinterpret_cast<char *>(tile2);
+    uint32_t o = ob;
+#pragma unroll
+    for (int g = 0; g < NA; ++g) {
+      const int j = g ^ (g >> 1);
+      if ((g & 7) == 0) {
+        o = ob;
+#pragma unroll
+        for (int k = 0; k < RB; ++k)
+          if ((j >> k) & 1) o ^= mb[k];
+      } else {
+        o ^= mb[ctz6(g)];
+      }
+      *reinterpret_cast<u64 *>(tw + o) = P[j];
+    }
+  }
+}
+
 // The pass's phases on one tile in shared memory, run by the 2^lognt threads
 // tid of its group; `sync` is the group's barrier, sH/sQ/sOut the group's
-// diagonal-phase scratch, s_w the all-site scratch (SITES only).
-template <int RB, bool SITES, typename Sync>
+// diagonal-phase scratch, s_w the all-site scratch (SITES only).  ORIENT: the
+// program and the state are oriented (see Orientation).
+template <int RB, bool SITES, bool ORIENT, typename Sync>
 __device__ __forceinline__ void run_phases(float2 *tile2, const PassDesc &d, const PhaseDesc *s_ph,
                                            const ROpRes *s_op, uint64_t base, int tid, int lognt, int M,
                                            const uint64_t *__restrict__ qdiag, float &up, float &dn,
                                            uint64_t *sH, uint64_t *sQ, uint64_t *sOut, double *s_w,
                                            Sync sync) {
   constexpr int NA = 1 << RB, NP = NA / 2;
-  const int K = d.K, nt = 1 << lognt;
-  const int nout = M - K;
+  const uint32_t outer_par = ORIENT ? (uint32_t)(__popcll(base & d.black_outer) & 1) : 0u;
   for (int p = 0; p < d.nphases; ++p) {
     const PhaseDesc &ph = s_ph[p];
     // slot of this thread's subcube origin (host-precomputed slot of each
@@ -886,97 +1196,11 @@ __device__ __forceinline__ void run_phases(float2 *tile2, const PassDesc &d, con
     for (int k = 0; k < RB; ++k) sm[k] = ph.sm[k];
     const int o0 = ph.op0 - d.rop0;
     if (ph.nops == 1 && s_op[o0].kind == OP_DIAG) {
-      // diagonal phase e^{-i tau D}, amplitude by amplitude in shared memory:
-      // Theta(x) = sum_{p<p'} q_pp' sigma_p sigma_p' (mod 2^64) split into
-      // outer-outer (sOut), outer-tile (sH) and tile-tile (sQ) parts
-      uint32_t t0 = 0;
-      for (int k = 0; k < 5; ++k) t0 |= ((uint32_t)(tid >> k) & 1u) << ph.lanes[k];
-      for (int k = 0; k < lognt - 5; ++k) t0 |= ((uint32_t)(tid >> (5 + k)) & 1u) << ph.warps[k];
-      const uint64_t *q = qdiag + (size_t)s_op[o0].arg * M * M;
-      if (tid < K) {
-        const int pp = d.tile_pos[tid];
-        uint64_t h = 0;
-        for (int o = 0; o < nout; ++o) {
-          const int po = d.outer_pos[o];
-          const uint64_t v = q[pp * M + po];
-          h += ((base >> po) & 1ull) ? v : (0ull - v);
-        }
-        sH[tid] = h;
-      } else if (tid == K) {
-        uint64_t s = 0;
-        for (int o = 0; o < nout; ++o)
-          for (int o2 = o + 1; o2 < nout; ++o2) {
-            const int pa = d.outer_pos[o], pb = d.outer_pos[o2];
-            const uint64_t v = q[pa * M + pb];
-            s += (((base >> pa) ^ (base >> pb)) & 1ull) ? (0ull - v) : v;
-          }
-        *sOut = s;
-      }
-      for (int w = tid; w < K * K; w += nt) sQ[w] = q[d.tile_pos[w / K] * M + d.tile_pos[w % K]];
-      sync();
-      uint32_t isreg = 0;
-      for (int k = 0; k < RB; ++k) isreg |= 1u << ph.rb[k];
-      // fixed part (tile bits from the thread index) once per thread
-      uint64_t th0 = *sOut;
-      for (int x = 0; x < K; ++x) {
-        if ((isreg >> x) & 1u) continue;
-        const uint32_t bx = (t0 >> x) & 1u;
-        th0 += bx ? sH[x] : (0ull - sH[x]);
-        for (int y = x + 1; y < K; ++y) {
-          if ((isreg >> y) & 1u) continue;
-          th0 += (bx ^ ((t0 >> y) & 1u)) ? (0ull - sQ[x * K + y]) : sQ[x * K + y];
-        }
-      }
-      // field on each register bit from the fixed bits, once per thread
-      uint64_t G[RB];
-#pragma unroll
-      for (int k = 0; k < RB; ++k) {
-        const int rk = ph.rb[k];
-        uint64_t g = sH[rk];
-        for (int x = 0; x < K; ++x) {
-          if ((isreg >> x) & 1u) continue;
-          g += ((t0 >> x) & 1u) ? sQ[x * K + rk] : (0ull - sQ[x * K + rk]);
-        }
-        G[k] = g;
-      }
-      // the register combinations in Gray-code order: with sigma_k = +1 for a
-      // set bit and -1 for a clear one, Theta = th0 + sum_k sigma_k G_k +
-      // sum_{k<l} sigma_k sigma_l Q_kl; flipping bit k changes Theta by
-      // -2 sigma_k F_k, F_k = G_k + sum_{l!=k} sigma_l Q_kl its field, and
-      // every other field F_l by -2 sigma_k Q_kl (exact, modulo 2^64)
-      uint64_t Qr[RB][RB], F[RB];
-#pragma unroll
-      for (int k = 0; k < RB; ++k)
-#pragma unroll
-        for (int l = 0; l < RB; ++l)
-          Qr[k][l] = k == l ? 0ull : sQ[ph.rb[k < l ? k : l] * K + ph.rb[k < l ? l : k]];
-      uint64_t th = th0;
-#pragma unroll
-      for (int k = 0; k < RB; ++k) {
-        th -= G[k];
-        F[k] = G[k];
-#pragma unroll
-        for (int l = 0; l < RB; ++l) {
-          if (l == k) continue;
-          F[k] -= Qr[k][l];
-          if (l > k) th += Qr[k][l];
-        }
-      }
-      uint32_t s = s0;
-#pragma unroll
-      for (int g = 0; g < NA; ++g) {
-        if (g) {
-          const int k = ctz6(g);
-          // sigma_k before the flip: +1 when the bit is set in gray(g - 1)
-          const bool was_up = ((((g - 1) ^ ((g - 1) >> 1)) >> k) & 1) != 0;
-          th += was_up ? (0ull - 2ull * F[k]) : 2ull * F[k];
-#pragma unroll
-          for (int l = 0; l < RB; ++l)
-            if (l != k) F[l] += was_up ? (0ull - 2ull * Qr[l][k]) : 2ull * Qr[l][k];
-          s ^= sm[k];
-        }
-        tile2[s] = cmul(tile2[s], cis_turns(th, 0.0f));
-      }
+      diag_phase<RB, ORIENT>(tile2, d, ph, s_op[o0], base, tid, lognt, M, qdiag, sH, sQ, sOut, s0, sm, sync);
+      continue;
+    }
+    if constexpr (ORIENT) {
+      oriented_phase<RB, SITES>(tile2, d, ph, s_op + o0, base, tid, lognt, up, dn, s_w, s0, sm, outer_par);
       sync();
       continue;
     }
@@ -1147,8 +1371,9 @@ __device__ __forceinline__ void store_tile(float2 *psi, uint64_t base, const Pas
 }  // namespace sw2
 
 // Register-blocked sweep with RB register bits (2^RB amplitudes per thread,
-// 2^(K-RB) threads per tile), one tile per block.
-template <int RB, bool SITES>
+// 2^(K-RB) threads per tile), one tile per block.  ORIENT: an oriented
+// program on an oriented state (see Orientation).
+template <int RB, bool SITES, bool ORIENT>
 __global__ void __launch_bounds__(RB == 5 ? 512 : 256)
 sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops1,
               const __grid_constant__ PassDesc d, const PhaseDesc *__restrict__ phases, int M,
@@ -1189,8 +1414,8 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops
   __syncthreads();
 
   float up = 0.f, dn = 0.f;
-  sw2::run_phases<RB, SITES>(tile2, d, s_ph, s_op, base, tid, lognt, M, jp.qdiag, up, dn, sH, sQ, &sOut, s_w,
-                             sw2::SyncBlock{});
+  sw2::run_phases<RB, SITES, ORIENT>(tile2, d, s_ph, s_op, base, tid, lognt, M, jp.qdiag, up, dn, sH, sQ,
+                                     &sOut, s_w, sw2::SyncBlock{});
   sw2::store_tile<RB>(psi, base, d, tid, lognt, tile2);
   if constexpr (SITES)
     if (d.has_reduce) write_site_partials(d, M, base, s_w, jp.psites);

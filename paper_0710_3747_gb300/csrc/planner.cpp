@@ -279,8 +279,29 @@ int phase_closure(const std::vector<std::pair<int, int>> &g, const std::vector<s
 
 }  // namespace
 
+// Every combination of `take` out of the n items (indices), in lexicographic
+// order, passed to f as a bit mask over items[].
+template <typename F>
+static void for_each_subset(const std::vector<int> &items, int take, F f) {
+  const int n = (int)items.size();
+  if (take > n || take < 0) return;
+  std::vector<int> pick(take);
+  for (int i = 0; i < take; ++i) pick[i] = i;
+  while (true) {
+    uint32_t R = 0;
+    for (int i : pick) R |= 1u << items[i];
+    f(R);
+    int i = take - 1;
+    while (i >= 0 && pick[i] == n - take + i) --i;
+    if (i < 0) break;
+    ++pick[i];
+    for (int j = i + 1; j < take; ++j) pick[j] = pick[j - 1] + 1;
+  }
+}
+
 bool plan_phases(int K, const std::vector<std::pair<int, int>> &gates, int RB, int beam, int fence,
-                 std::vector<uint32_t> *sets, std::vector<std::vector<int>> *applied) {
+                 std::vector<uint32_t> *sets, std::vector<std::vector<int>> *applied, uint32_t black,
+                 uint32_t nb_allowed) {
   sets->clear();
   applied->clear();
   const int n = (int)gates.size();
@@ -308,25 +329,41 @@ bool plan_phases(int K, const std::vector<std::pair<int, int>> &gates, int RB, i
       std::vector<int> live;
       for (int q = 0; q < K; ++q)
         if (st.ptr[q] < chain[q].size()) live.push_back(q);
-      const int take = std::min<int>(RB, (int)live.size());
-      std::vector<int> pick(take);
-      for (int i = 0; i < take; ++i) pick[i] = i;
-      while (true) {
-        uint32_t R = 0;
-        for (int i : pick) R |= 1u << live[i];
-        for (int q = 0; q < K && __builtin_popcount(R) < RB; ++q) R |= 1u << q;
+      auto try_set = [&](uint32_t R) {
         PhaseState ch{st.ptr, st.done, st.pre, si, R};
         const int a = phase_closure(gates, chain, ch.ptr, R, fence, &ch.pre, nullptr);
         if (a > 0) {
           ch.done += a;
           next.push_back(std::move(ch));
         }
-        // next combination of `take` out of live.size()
-        int i = take - 1;
-        while (i >= 0 && pick[i] == (int)live.size() - take + i) --i;
-        if (i < 0) break;
-        ++pick[i];
-        for (int j = i + 1; j < take; ++j) pick[j] = pick[j - 1] + 1;
+      };
+      if (nb_allowed == 0) {
+        const int take = std::min<int>(RB, (int)live.size());
+        for_each_subset(live, take, [&](uint32_t R) {
+          for (int q = 0; q < K && __builtin_popcount(R) < RB; ++q) R |= 1u << q;
+          try_set(R);
+        });
+      } else {
+        // for each allowed count nb: nb live bits of the colour `black` and
+        // RB - nb of the other (fewer when fewer are live), each side padded
+        // with idle bits of its colour
+        std::vector<int> lb, lw;
+        for (int q : live) (((black >> q) & 1u) ? lb : lw).push_back(q);
+        for (int nb = 0; nb <= RB; ++nb) {
+          if (!((nb_allowed >> nb) & 1u)) continue;
+          const int tb = std::min<int>(nb, (int)lb.size()), tw = std::min<int>(RB - nb, (int)lw.size());
+          for_each_subset(lb, tb, [&](uint32_t Rb) {
+            for (int q = 0; q < K && __builtin_popcount(Rb) < nb; ++q)
+              if ((black >> q) & 1u) Rb |= 1u << q;
+            if (__builtin_popcount(Rb) != nb) return;
+            for_each_subset(lw, tw, [&](uint32_t Rw) {
+              for (int q = 0; q < K && __builtin_popcount(Rw) < RB - nb; ++q)
+                if (!((black >> q) & 1u)) Rw |= 1u << q;
+              if (__builtin_popcount(Rw) != RB - nb) return;
+              try_set(Rb | Rw);
+            });
+          });
+        }
       }
     }
     if (next.empty()) return false;

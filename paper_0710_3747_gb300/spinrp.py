@@ -68,6 +68,8 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             "spinrp_system_bonds": ([vp, i32p, ctypes.c_int, ip], ctypes.c_int),
             "spinrp_system_set_tile": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
             "spinrp_system_set_regbits": ([vp, ctypes.c_int], ctypes.c_int),
+            "spinrp_system_set_orientation": ([vp, ctypes.c_int], ctypes.c_int),
+            "spinrp_state_orientation": ([vp, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
             "spinrp_system_plan_info": ([vp, ctypes.c_int, ip, ip, ip], ctypes.c_int),
             "spinrp_system_plan_gates": ([vp, ctypes.c_int, i32p, i32p, ctypes.c_int, ip], ctypes.c_int),
             "spinrp_state_bytes": ([vp, ctypes.c_int, ctypes.c_int64, szp, szp], ctypes.c_int),
@@ -221,6 +223,11 @@ class System:
         """Register bits per phase of the complex64 kernel (5 or 6; 0 = default)."""
         _check(lib().spinrp_system_set_regbits(self._h, int(rb)))
 
+    def set_orientation(self, mode: int):
+        """1 (default): complex64 states of a bipartite system are stored
+        oriented (see include/spinrp.h); 0: always plainly."""
+        _check(lib().spinrp_system_set_orientation(self._h, int(mode)))
+
     def plan_info(self, prec="c64") -> dict:
         s, w, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().spinrp_system_plan_info(self._h, _PREC[prec], ctypes.byref(s), ctypes.byref(w),
@@ -364,6 +371,14 @@ class State:
         p = ctypes.c_void_p()
         _check(lib().spinrp_state_layout(self._h, lay, ctypes.byref(p)))
         return list(lay)
+
+    def orientation(self) -> int:
+        """Mask of first-colour spins (bit q-1 = spin q) of an oriented state,
+        whose amplitudes with an odd number of them up are stored (Im, Re);
+        0 for a plainly stored state."""
+        m = ctypes.c_uint64()
+        _check(lib().spinrp_state_orientation(self._h, ctypes.byref(m)))
+        return int(m.value)
 
     def device_ptr(self) -> int:
         """Device address of the amplitude buffer."""

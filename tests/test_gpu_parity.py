@@ -292,25 +292,42 @@ def test_star_m20_fp64_and_fp32():
 
 @pytest.mark.slow
 def test_ladder_m30_sampled():
-    """2x15 ladder at full size (2^30 amplitudes, 8 GiB c64 / 16 GiB c128):
-    the first Trotter step against the oracle (P, norm and 2^14 sampled
-    amplitudes) for both precisions, then the invariants over 20 steps."""
+    """2x15 ladder at full size (2^30 amplitudes, 8 GiB c64 / 16 GiB c128), in
+    the bench's launch configuration: five Trotter steps against the oracle
+    (P and norm after every step, 2^14 sampled amplitudes at the end) for both
+    precisions -- the first, three steady and the last step's sweeps -- then
+    20 more steps as CUDA-graph replays, which must equal the same steps as
+    direct launches bit for bit, and the invariants."""
     job = W.ladder_m30()
+    steps = 5
     idx = np.random.default_rng(1).integers(0, 1 << 30, size=1 << 14)
-    Pw, Nw, psi_w = _oracle(job.J, job.htype, job.seed, job.dt, 1)
+    Pw, Nw, psi_w = _oracle(job.J, job.htype, job.seed, job.dt, steps)
     ref = psi_w[idx].copy()
     del psi_w
     for prec in ("c64", "c128"):
-        st = spinrp.State(spinrp.System(job.J, job.htype), prec, series_cap=32)
+        st = spinrp.State(spinrp.System(job.J, job.htype), prec, series_cap=64)
         st.init_random_phase(job.seed)
-        st.evolve(job.dt, 1)
+        st.evolve(job.dt, steps)
         got = st.read(idx)
-        Pg = st.polarization()
+        Pg, Ng = st.polarization(), st.norm_series()
         assert np.max(np.abs(Pg - Pw)) <= TOL_P[prec], prec
-        # FP32: ~86 roundings per amplitude in one step, max over 2^14 samples
-        tol = 1e-12 if prec == "c128" else 4e-6 * 2.0 ** -14.5
+        assert np.max(np.abs(Ng - Nw)) <= (1e-12 if prec == "c128" else 1e-6), prec
+        # FP32: ~86 roundings per amplitude and step, max over 2^14 samples
+        tol = 1e-12 if prec == "c128" else 1e-5 * 2.0 ** -14.5
         assert np.max(np.abs(got - ref)) < tol, prec
-        st.evolve(job.dt, 19)
+        # 20 steady steps replayed from a graph against the same steps launched
+        # directly (profiling turns graphs off) on a copy of the state
+        amp_idx = np.random.default_rng(2).integers(0, 1 << 30, size=1 << 12)
+        st2 = spinrp.State(spinrp.System(job.J, job.htype), prec, series_cap=64)
+        st2.init_random_phase(job.seed)
+        st2.evolve(job.dt, steps)
+        st.evolve(job.dt, 20)
+        st2.profile(True)
+        st2.evolve(job.dt, 20)
+        st2.profile(False)
+        assert np.array_equal(st.polarization(), st2.polarization()), prec
+        assert np.array_equal(st.read(amp_idx), st2.read(amp_idx)), prec
+        st2.close()
         N = st.norm_series()
         assert np.max(np.abs(N - 1.0)) < (1e-10 if prec == "c128" else 1e-5)
         P = st.polarization()
@@ -320,6 +337,24 @@ def test_ladder_m30_sampled():
         want = np.array([0.0] + [math.comb(29, k - 1) / 2.0 ** 29 for k in range(1, 31)])
         assert np.max(np.abs(n - want)) < (1e-12 if prec == "c128" else 2e-5), prec
         st.close()
+
+
+@pytest.mark.slow
+def test_fp32_against_fp64_over_200_steps_m30():
+    """The bench's workload (2x15 ladder, 2^30 amplitudes, dt 0.05, 200
+    steps): P(t) of the FP32 path against the FP64 path (held to 1e-10 of the
+    oracle over its first steps above) at every one of the 201 entries."""
+    job = W.ladder_m30()
+    P = {}
+    for prec in ("c64", "c128"):
+        st = spinrp.State(spinrp.System(job.J, job.htype), prec, series_cap=job.steps + 1)
+        st.init_random_phase(job.seed).evolve(job.dt, job.steps)
+        P[prec] = st.polarization()
+        st.close()
+    assert len(P["c64"]) == job.steps + 1
+    err = float(np.max(np.abs(P["c64"] - P["c128"])))
+    print(f"max |P_fp32 - P_fp64| over {job.steps} steps, M = 30: {err:.3e}")
+    assert err <= 1e-5
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
@@ -398,3 +433,97 @@ def test_fp32_error_over_200_steps_m26():
     err = float(np.max(np.abs(P["c64"] - P["c128"])))
     print(f"max |P_fp32 - P_fp64| over {steps} steps, M = 26: {err:.3e}")
     assert err <= 1e-5
+
+
+# ---------------------------------------------------------------------------
+# oriented storage (complex64 states of bipartite systems)
+def _xy_ising_ladder(L):
+    J = W.ladder(L, 1.0, 0.6)
+    a = 0.7 * W.ladder(L, 1.0, 0.4) + 0.2 * np.eye(2 * L)[::-1]
+    a = 0.5 * (a + a.T)
+    np.fill_diagonal(a, 0.0)
+    return J, a
+
+
+def test_orientation_is_used_where_it_applies():
+    """Ladders and chains (bipartite flip-flop graphs) get oriented complex64
+    states in the register-blocked kernel; stars, complex128 states and
+    systems set to plain storage do not."""
+    lad = spinrp.System(W.ladder(8, 1.0, 0.5), spinrp.XY)
+    lad.set_tile("c64", 13)
+    st = spinrp.State(lad, "c64", series_cap=2)
+    black = st.orientation()
+    assert black != 0
+    # every bond joins the two colours
+    for i, j in lad.bonds():
+        assert ((black >> i) & 1) != ((black >> j) & 1)
+    st.close()
+    assert spinrp.State(lad, "c128", series_cap=2).orientation() == 0
+    star = spinrp.System(W.star_dipolar(16, 8), spinrp.DIPOLAR)
+    star.set_tile("c64", 13)
+    assert spinrp.State(star, "c64", series_cap=2).orientation() == 0
+    lad.set_orientation(0)
+    assert spinrp.State(lad, "c64", series_cap=2).orientation() == 0
+
+
+@pytest.mark.parametrize("rb,K", [(5, 11), (5, 12), (6, 12), (6, 13), (6, 14)])
+@pytest.mark.parametrize("kind", ["ladder18", "chain19", "xy_ising_ladder16"])
+def test_oriented_and_plain_storage_match_oracle(kind, rb, K):
+    """The oriented and the plain register-blocked programs on the same
+    bipartite system, both against the oracle (P every step, every
+    amplitude); with S^zS^z terms the oriented diagonal phase is exercised."""
+    a = None
+    if kind == "ladder18":
+        J, ht = W.ladder(9, 1.0, 0.5), spinrp.XY
+    elif kind == "chain19":
+        J, ht = W.chain(19, 0.8), spinrp.XY
+    else:
+        J, a = _xy_ising_ladder(8)
+        ht = spinrp.GENERIC
+    seed, dt, steps = 21, 0.05, 6
+    Pw, Nw, psi_w = _oracle(J, ht, seed, dt, steps, a)
+    res = {}
+    for mode in (1, 0):
+        s = spinrp.System(J, ht, a)
+        s.set_tile("c64", K)
+        s.set_regbits(rb)
+        s.set_orientation(mode)
+        st = spinrp.State(s, "c64", series_cap=steps + 1)
+        assert (st.orientation() != 0) == (mode == 1), (kind, mode)
+        st.init_random_phase(seed).evolve(dt, steps)
+        P = st.polarization()
+        assert np.max(np.abs(P - Pw)) <= 1e-5, (kind, mode)
+        assert np.max(np.abs(st.norm_series() - Nw)) <= 1e-5, (kind, mode)
+        amp = st.amplitudes()
+        assert np.max(np.abs(amp - psi_w)) <= 2e-6 * 2.0 ** (-(st.M - 1) / 2) * 64, (kind, mode)
+        res[mode] = P
+        st.close()
+    assert np.max(np.abs(res[1] - res[0])) <= 1e-6
+
+
+def test_oriented_buffer_layout():
+    """An oriented state's raw buffer holds amplitude x at its physical index
+    as (Re, Im) when x has an even number of first-colour spins up and as
+    (Im, Re) when odd; spinrp_state_read undoes the swap."""
+    J = W.ladder(7, 1.0, 0.5)
+    s = spinrp.System(J, spinrp.XY)
+    s.set_tile("c64", 12)
+    st = spinrp.State(s, "c64", series_cap=4)  # amplitude buffer from PyTorch
+    st.init_random_phase(9).evolve(0.05, 3)
+    black, lay = st.orientation(), st.layout()
+    assert black != 0
+    M = st.M
+    idx = np.arange(1 << M)
+    want = st.read(idx)
+    psi_buf = st._bufs[0]
+    assert psi_buf.data_ptr() == st.device_ptr()
+    w = psi_buf.cpu().numpy().view(np.float32).reshape(-1, 2)
+    phys = np.zeros_like(idx)
+    for q in range(M):
+        phys |= ((idx >> q) & 1) << lay[q]
+    odd = np.array([bin(int(x) & black).count("1") & 1 for x in idx], dtype=bool)
+    re = np.where(odd, w[phys, 1], w[phys, 0])
+    im = np.where(odd, w[phys, 0], w[phys, 1])
+    assert np.max(np.abs((re + 1j * im) - want)) < 1e-7
+    assert np.any(odd) and np.any(~odd)
+    st.close()
