@@ -946,6 +946,10 @@ static void free_state(spinrp_state *st) {
   delete st;
 }
 
+// Largest dynamic shared memory of resident_kernel: 227 KiB per block less
+// its static arrays (diagonal-phase and reduction scratch, under 4 KiB).
+constexpr size_t kResidentMaxSmem = size_t(223) * 1024;
+
 template <typename R>
 static int set_smem_limits() {
   // the widest tile of this precision (2^14 c64 or 2^13 c128 = 128 KiB)
@@ -964,6 +968,10 @@ static int set_smem_limits() {
     CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6, false, true>, a, 8 << 14));
     CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<5, true, true>, a, 8 << 14));
     CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6, true, true>, a, 8 << 14));
+    CUDA_TRY(cudaFuncSetAttribute(resident_kernel<5, false>, a, (int)kResidentMaxSmem));
+    CUDA_TRY(cudaFuncSetAttribute(resident_kernel<5, true>, a, (int)kResidentMaxSmem));
+    CUDA_TRY(cudaFuncSetAttribute(resident_kernel<6, false>, a, (int)kResidentMaxSmem));
+    CUDA_TRY(cudaFuncSetAttribute(resident_kernel<6, true>, a, (int)kResidentMaxSmem));
   } else {
     CUDA_TRY(cudaFuncSetAttribute(sweep2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 << 13));
   }
@@ -1292,8 +1300,51 @@ struct LaunchCtx {
   bool oriented = false;         // oriented program and state (complex64)
   int sites = 0;                 // all-site readout after every reducing sweep
   unsigned prefetch_ahead = 0;   // sweep blocks resident at once (L2 prefetch distance), 0 = off
+  bool resident = false;         // whole state kept in shared memory for every step (resident_kernel)
+  size_t resident_smem = 0;      // its dynamic shared memory
   spinrp_state *prof = nullptr;  // state whose profiling marks to record, if any
 };
+
+// Dynamic shared memory of resident_kernel for a plan, or 0 when the plan
+// cannot run resident: complex64, one tile holding the whole state (one
+// segment, register-blocked program), no all-site readout, and the state plus
+// the program within the 227 KiB a block may use.
+static size_t resident_bytes(const Plan &plan, const PassSet &ps, int prec, bool sites) {
+  if (prec != SPINRP_C64 || !ps.phased || plan.segments() != 1 || plan.K != plan.M || sites) return 0;
+  if (ps.only < 0 || ps.first < 0 || ps.midstep < 0 || ps.last < 0) return 0;
+  const size_t b = (size_t(8) << plan.M) + sizeof(PhaseDesc) * ps.phases.size() +
+                   sizeof(ROpRes) * ps.rops.size();
+  return b <= kResidentMaxSmem ? b : 0;
+}
+
+// All steps of an evolve call of a resident context: one launch.
+static int launch_resident(const LaunchCtx &c, cudaStream_t stream, int64_t steps, bool live) {
+  ResidentPasses rp;
+  rp.first = c.ps->desc[c.ps->first];
+  rp.mid = c.ps->desc[c.ps->midstep];
+  rp.last = c.ps->desc[c.ps->last];
+  rp.only = c.ps->desc[c.ps->only];
+  const int nph = (int)c.ps->phases.size(), nrops = (int)c.ps->rops.size();
+  const dim3 grid(1, (unsigned)c.njobs);
+  const unsigned nt = 1u << (c.M - c.rb);
+  if (live) {
+    if (c.prof) prof_mark(c.prof, SPINRP_KERNEL_SWEEP);
+    ++g_launches;
+  }
+  const int code = (c.rb == 6 ? 2 : 0) | (c.oriented ? 1 : 0);
+#define RES(RB_, O_) \
+  resident_kernel<RB_, O_><<<grid, nt, c.resident_smem, stream>>>(c.jobs, rp, c.phases, nph, nrops, c.M, steps)
+  switch (code) {
+    case 0: RES(5, false); break;
+    case 1: RES(5, true); break;
+    case 2: RES(6, false); break;
+    default: RES(6, true); break;
+  }
+#undef RES
+  CUDA_TRY(cudaGetLastError());
+  if (live && c.prof) prof_mark(c.prof, SPINRP_KERNEL_SWEEP);
+  return SPINRP_OK;
+}
 
 // Launch one sweep on `stream`; `live` launches are counted and profiled,
 // launches recorded into a graph are not.
@@ -1434,8 +1485,18 @@ static int capture_graph(const std::vector<LaunchCtx> &cs, cudaStream_t *cap_str
 // `steps` Trotter steps of every context (all share dt and steps): the first
 // step, the steady steps (as graph replays when `use_graph`), the last step.
 template <typename R>
-static int run_steps(const std::vector<LaunchCtx> &cs, cudaStream_t stream, int64_t steps,
+static int run_steps(const std::vector<LaunchCtx> &all, cudaStream_t stream, int64_t steps,
                      bool use_graph, cudaStream_t *cap_stream, cudaGraphExec_t *graph) {
+  // resident contexts run every step in one launch
+  std::vector<LaunchCtx> cs;
+  for (const LaunchCtx &c : all) {
+    if (!c.resident) {
+      cs.push_back(c);
+      continue;
+    }
+    int rc = launch_resident(c, stream, steps, true);
+    if (rc) return rc;
+  }
   for (const LaunchCtx &c : cs) {
     int rc = first_step<R>(c, stream, steps, true);
     if (rc) return rc;
@@ -1482,6 +1543,8 @@ static LaunchCtx state_ctx(spinrp_state *st) {
   c.rb = st->ps.rb;
   c.oriented = st->ps.oriented;
   c.sites = st->sites ? 1 : 0;
+  c.resident_smem = resident_bytes(st->plan, st->ps, st->prec, st->sites);
+  c.resident = c.resident_smem > 0;
   c.prefetch_ahead = st->prefetch_ahead;
   c.segments = st->plan.segments();
   c.sweeps_per_step = st->plan.sweeps_per_step();
@@ -2255,7 +2318,7 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
     g.M = s0.M;
     g.nb = (int)s0.bonds.size();
     g.has_diag = any_diag(s0);
-    int rc = plan_state(s0, prec, &g.plan, &g.ps, &g.max_blocks, (int)g.jobs.size(), false);
+    int rc = plan_state(s0, prec, &g.plan, &g.ps, &g.max_blocks, (int)g.jobs.size());
     if (rc) {
       free_batch(b);
       return rc;
@@ -2348,6 +2411,9 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
     c.jobs = g.d_jobs;
     if (n == 1) c.job0 = hj[0];
     c.njobs = n;
+    c.oriented = g.ps.oriented;
+    c.resident_smem = resident_bytes(g.plan, g.ps, prec, false);
+    c.resident = c.resident_smem > 0;
 
   }
   // the LaunchCtx keep pointers to their group's PassSet: fix them now that
@@ -2373,7 +2439,7 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
     return rc;
   }
   for (BatchGroup &g : b->groups)
-    if (g.ps.phased) g.ctx.prefetch_ahead = sweep2_resident(prec, g.ps.rb, g.plan.K, false);
+    if (g.ps.phased) g.ctx.prefetch_ahead = sweep2_resident(prec, g.ps.rb, g.plan.K, g.ps.oriented);
   *out = b;
   return SPINRP_OK;
 }
@@ -2404,7 +2470,8 @@ static int batch_init(spinrp_batch *b, int kind) {
     const dim3 grid(init_blocks(g.M), (unsigned)g.jobs.size());
     ++g_launches;
     if (b->prec == SPINRP_C64)
-      init_kernel<float><<<grid, 256, 0, b->stream>>>(g.d_jobs, g.M, group_layout(g), 0, g.d_seeds, kind, 0);
+      init_kernel<float><<<grid, 256, 0, b->stream>>>(g.d_jobs, g.M, group_layout(g), 0, g.d_seeds, kind,
+                                                      g.ps.oriented ? g.ps.black : 0ull);
     else
       init_kernel<double><<<grid, 256, 0, b->stream>>>(g.d_jobs, g.M, group_layout(g), 0, g.d_seeds, kind, 0);
     CUDA_TRY(cudaGetLastError());

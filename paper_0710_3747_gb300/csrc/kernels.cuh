@@ -1422,4 +1422,74 @@ sweep2_kernel(const JobPtrs *__restrict__ jobs, float2 *psi1, const ROpRes *sops
   if (d.has_reduce) reduce_finalize((double)up, (double)dn, jp, false);
 }
 
+// ===========================================================================
+// Whole states resident in shared memory.  When one tile holds the whole
+// state (K = M, one segment), every Trotter step is one pass over that tile,
+// so a block can keep the state in shared memory for all the steps of an
+// evolve call: one global load at the start, one store at the end, and the
+// P / norm readout after every step reduced inside the block.
+// ===========================================================================
+// The four passes of a one-tile plan: the first, steady and last step of an
+// evolve call of two or more steps, and the step of a one-step call.
+struct ResidentPasses {
+  PassDesc first, mid, last, only;
+};
+
+// One block per job (blockIdx.y); 2^(M-RB) threads.  Dynamic shared memory:
+// the state (8 B x 2^M), then the plan's phase program (nph PhaseDesc) and its
+// resolved ops (nrops ROpRes).  ORIENT: oriented program and state.
+template <int RB, bool ORIENT>
+__global__ void __launch_bounds__(256)
+resident_kernel(const JobPtrs *__restrict__ jobs, const __grid_constant__ ResidentPasses rp,
+                const PhaseDesc *__restrict__ phases, int nph, int nrops, int M, int64_t steps) {
+  const JobPtrs jp = jobs[blockIdx.y];
+  float2 *__restrict__ psi = static_cast<float2 *>(jp.psi);
+  extern __shared__ __align__(16) float2 tile2[];
+  PhaseDesc *s_ph = reinterpret_cast<PhaseDesc *>(tile2 + (size_t(1) << M));
+  ROpRes *s_op = reinterpret_cast<ROpRes *>(s_ph + nph);
+  __shared__ uint64_t sH[kMaxK];
+  __shared__ uint64_t sQ[kMaxK * kMaxK];
+  __shared__ uint64_t sOut;
+  __shared__ double s_up[8], s_dn[8];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lognt = M - RB;
+  // the state (tile bits = physical bits: base 0, no relabelling), then the program
+  sw2::load_tile<RB>(psi, 0, rp.first, tid, lognt, (uint32_t)__cvta_generic_to_shared(tile2));
+  {
+    const uint32_t *pw = reinterpret_cast<const uint32_t *>(phases);
+    const uint32_t a_ph = (uint32_t)__cvta_generic_to_shared(s_ph);
+    const int nw = nph * (int)(sizeof(PhaseDesc) / 4);
+    for (int i = tid; i < nw; i += nt) sw2::cp_async4(a_ph + 4u * i, pw + i);
+    const uint32_t a_op = (uint32_t)__cvta_generic_to_shared(s_op);
+    for (int i = tid; i < nrops; i += nt) sw2::cp_async16(a_op + 16u * i, jp.sops + i);
+  }
+  sw2::cp_async_wait_all();
+  __syncthreads();
+  const int64_t slot0 = *jp.step;
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  for (int64_t k = 0; k < steps; ++k) {
+    const PassDesc &d = steps == 1 ? rp.only : k == 0 ? rp.first : k == steps - 1 ? rp.last : rp.mid;
+    float up = 0.f, dn = 0.f;
+    sw2::run_phases<RB, false, ORIENT>(tile2, d, s_ph + d.phase0, s_op + d.rop0, 0ull, tid, lognt, M,
+                                       jp.qdiag, up, dn, sH, sQ, &sOut, nullptr, sw2::SyncBlock{});
+    // this step's N_up / N_dn: FP64 sums over the block in a fixed order
+    double u = up, w = dn;
+    for (int o = 16; o; o >>= 1) {
+      u += __shfl_xor_sync(0xffffffffu, u, o);
+      w += __shfl_xor_sync(0xffffffffu, w, o);
+    }
+    if (lane == 0) s_up[warp] = u, s_dn[warp] = w;
+    __syncthreads();
+    if (tid == 0) {
+      double U = 0.0, D = 0.0;
+      for (int i = 0; i < nw; ++i) U += s_up[i], D += s_dn[i];
+      jp.series[2 * (slot0 + k)] = (U - D) / (U + D);
+      jp.series[2 * (slot0 + k) + 1] = U + D;
+    }
+    __syncthreads();
+  }
+  sw2::store_tile<RB>(psi, 0, rp.first, tid, lognt, tile2);
+  if (tid == 0) *jp.step = slot0 + steps;
+}
+
 }  // namespace spinrp

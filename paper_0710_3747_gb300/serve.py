@@ -53,6 +53,7 @@ class _Active:
     left: int
     bytes: int
     system: spinrp.System = field(repr=False, default=None)
+    events: list = field(default_factory=list)  # CUDA events of the chunks in flight
 
 
 def footprint(job: W.Job, prec: str) -> int:
@@ -61,9 +62,25 @@ def footprint(job: W.Job, prec: str) -> int:
     return p + w
 
 
-def _start(job: W.Job, prec: str, now: float, tile_K: int | None) -> _Active:
+def job_work(job: W.Job) -> float:
+    """Amplitude-gate updates of the whole job (2^M x 2 bonds x steps)."""
+    nb = int(np.count_nonzero(np.triu(job.J, 1)))
+    return float(2 ** job.M) * 2 * nb * job.steps
+
+
+# Stream priority of a job by its size: work below 10^10 amplitude-gate
+# updates (milliseconds on the GPU) gets the highest priority, below 10^12
+# (well under a second) the next, the rest the lowest.  The GPU's block
+# scheduler then serves short jobs first when streams compete, so a short job
+# arriving behind long ones is not queued behind their sweeps.
+def _priority(job: W.Job) -> int:
+    w = job_work(job)
+    return -2 if w < 1e10 else (-1 if w < 1e12 else 0)
+
+
+def _start(job: W.Job, prec: str, now: float, tile_K: int | None, priority: int = 0) -> _Active:
     import torch
-    stream = torch.cuda.Stream()
+    stream = torch.cuda.Stream(priority=priority)
     sysm = spinrp.System(job.J, job.htype)
     if tile_K:
         sysm.set_tile(prec, min(tile_K, job.M))
@@ -75,24 +92,40 @@ def _start(job: W.Job, prec: str, now: float, tile_K: int | None) -> _Active:
 
 
 def _finish(a: _Active, now_fn) -> Result:
-    a.res.P = a.state.polarization()      # synchronizes the job's stream
+    a.res.P = a.state.polarization()      # synchronizes the job's stream (already done)
     a.res.norm = a.state.norm_series()
     a.res.done = now_fn()
     a.state.close()
     return a.res
 
 
+def _chunk_done(a: _Active) -> bool:
+    """True when the oldest chunk in flight has finished on the device
+    (always for host-side fakes, which have no stream)."""
+    if not a.events:
+        return True
+    if a.events[0].query():
+        a.events.pop(0)
+        return True
+    return False
+
+
 def run_stream(jobs: list[W.Job], prec: str = "c64", max_active: int = 16,
                hbm_budget: int | None = None, chunk: int = 20, tile_K: int | None = None,
                realtime: bool = True, start_fn=None, finish_fn=None, footprint_fn=None,
-               trace: list | None = None) -> list[Result]:
+               trace: list | None = None, depth: int = 2, priorities: bool = True) -> list[Result]:
     """Serve `jobs` (sorted by arrival) with continuous batching.
 
     realtime: arrivals follow the wall clock (t = 0 at the call); otherwise all
     jobs are treated as arrived at their arrival offset but admitted as soon
-    as resources allow (a saturated queue).  start_fn / finish_fn /
-    footprint_fn replace the device calls (host-side tests); `trace`, when
-    given, receives ("admit" | "chunk" | "done", job index, bytes in use)."""
+    as resources allow (a saturated queue).  Each admitted job gets its own
+    CUDA stream (priority by job size when `priorities`); the loop keeps up to
+    `depth` chunks of `chunk` Trotter steps in flight per job, polls their
+    completion events without blocking, and retires a job (P(t) to the host,
+    memory and slot freed) as soon as its last chunk has finished.  Each job's
+    footprint is computed once.  start_fn / finish_fn / footprint_fn replace
+    the device calls (host-side tests); `trace`, when given, receives
+    ("admit" | "chunk" | "done", job index, bytes in use)."""
     footprint_fn = footprint_fn or footprint
     start_fn = start_fn or _start
     finish_fn = finish_fn or _finish
@@ -101,6 +134,7 @@ def run_stream(jobs: list[W.Job], prec: str = "c64", max_active: int = 16,
         free, _ = torch.cuda.mem_get_info()
         hbm_budget = int(0.8 * free)
     pending = sorted(jobs, key=lambda j: j.arrival)
+    need = {}
     active: list[_Active] = []
     done: list[Result] = []
     t0 = time.perf_counter()
@@ -108,44 +142,63 @@ def run_stream(jobs: list[W.Job], prec: str = "c64", max_active: int = 16,
     used = 0
     k = 0
     while k < len(pending) or active:
+        progress = False
         # admit arrived jobs while slots and memory allow
         while k < len(pending) and len(active) < max_active:
             j = pending[k]
             if realtime and j.arrival > now():
                 break
-            need = footprint_fn(j, prec)
-            if need > hbm_budget:
-                raise spinrp.SpinrpError(spinrp.ENOMEM, f"job {k} needs {need} B > budget {hbm_budget} B")
-            if used + need > hbm_budget:
+            if k not in need:
+                need[k] = footprint_fn(j, prec)
+                if need[k] > hbm_budget:
+                    raise spinrp.SpinrpError(spinrp.ENOMEM,
+                                             f"job {k} needs {need[k]} B > budget {hbm_budget} B")
+            if used + need[k] > hbm_budget:
                 break
-            a = start_fn(j, prec, now(), tile_K)
+            if start_fn is _start:
+                a = _start(j, prec, now(), tile_K, _priority(j) if priorities else 0)
+            else:
+                a = start_fn(j, prec, now(), tile_K)
             active.append(a)
             used += a.bytes
+            progress = True
             if trace is not None:
                 trace.append(("admit", a.res.index, used))
             k += 1
-        if not active:
-            # idle until the next arrival
-            if k < len(pending):
-                time.sleep(max(0.0, min(0.01, pending[k].arrival - now())))
-            continue
-        # one chunk of Trotter steps for every active job (each on its stream)
+        # keep up to `depth` chunks in flight per job
         for a in active:
-            n = min(chunk, a.left)
-            a.state.evolve(a.job.dt, n)
-            a.left -= n
-            if trace is not None:
-                trace.append(("chunk", a.res.index, used))
+            while a.left > 0 and len(a.events) < depth:
+                n = min(chunk, a.left)
+                a.state.evolve(a.job.dt, n)
+                a.left -= n
+                if a.stream is not None:
+                    import torch
+                    ev = torch.cuda.Event()
+                    ev.record(a.stream)
+                    a.events.append(ev)
+                progress = True
+                if trace is not None:
+                    trace.append(("chunk", a.res.index, used))
+        # retire finished chunks and jobs
         still = []
         for a in active:
-            if a.left == 0:
+            while a.events and _chunk_done(a):
+                progress = True
+            if a.left == 0 and not a.events:
                 done.append(finish_fn(a, now))
                 used -= a.bytes
+                progress = True
                 if trace is not None:
                     trace.append(("done", a.res.index, used))
             else:
                 still.append(a)
         active = still
+        if not progress:
+            # idle: wait for the next arrival or completion
+            wait = 0.0002
+            if not active and k < len(pending):
+                wait = max(0.0, min(0.01, pending[k].arrival - now()))
+            time.sleep(wait)
     return sorted(done, key=lambda r: r.index)
 
 
@@ -189,6 +242,9 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--prec", default="c64")
     ap.add_argument("--tile-K", type=int, default=0, help="tile width for every job (0: the library's default)")
+    ap.add_argument("--saturated", action="store_true",
+                    help="every job arrives at t = 0 (a full queue): throughput is not bound by arrivals")
+    ap.add_argument("--no-priorities", action="store_true", help="all job streams at the default priority")
     args = ap.parse_args(argv)
     tile_K = args.tile_K or None
     import torch
@@ -200,15 +256,25 @@ def main(argv=None):
         run_sequential(probe, args.prec, tile_K=tile_K, realtime=False)
         rate = 0.7 * len(probe) / (time.perf_counter() - t)
     jobs = W.serve_stream(n=args.jobs, seed=args.seed, rate=rate, m_cap=args.m_cap)
+    realtime = not args.saturated
+    if args.saturated:
+        for j in jobs:
+            j.arrival = 0.0
     t = time.perf_counter()
-    mix = run_stream(jobs, args.prec, max_active=args.max_active, chunk=args.chunk, tile_K=tile_K)
+    mix = run_stream(jobs, args.prec, max_active=args.max_active, chunk=args.chunk, tile_K=tile_K,
+                     realtime=realtime, priorities=not args.no_priorities)
+    torch.cuda.synchronize()
     wall_mix = time.perf_counter() - t
     t = time.perf_counter()
-    seq = run_sequential(jobs, args.prec, tile_K=tile_K)
+    seq = run_sequential(jobs, args.prec, tile_K=tile_K, realtime=realtime)
     wall_seq = time.perf_counter() - t
     same = max(float(np.max(np.abs(a.P - b.P))) for a, b in zip(mix, seq))
-    print(json.dumps({"rate_per_s": rate, "continuous": summary(mix, wall_mix),
-                      "sequential": summary(seq, wall_seq), "max_dP_mix_vs_alone": same}))
+    work = sum(job_work(j) for j in jobs)
+    Ms = [j.M for j in jobs]
+    print(json.dumps({"jobs": len(jobs), "saturated": args.saturated, "rate_per_s": None if args.saturated else rate,
+                      "M_range": [min(Ms), max(Ms)], "amp_gate_updates": work,
+                      "continuous": summary(mix, wall_mix), "sequential": summary(seq, wall_seq),
+                      "max_dP_mix_vs_alone": same}))
     return 0
 
 

@@ -109,3 +109,46 @@ def test_mix_equals_alone_and_oracle():
     for r, j in list(zip(mix, jobs))[:4]:
         Pw, _, _ = oracle.run(j.J, j.htype, j.seed, j.dt, j.steps)
         assert np.max(np.abs(r.P - Pw)) <= 1e-4
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_full_stream_sampled_jobs_match_oracle():
+    """Twenty jobs with M <= 22 drawn at random from the full 2000-job request
+    stream (its seed and distributions: ladders and dipolar stars, M
+    log-uniform in 10..28, T in [5, 50]), served together through the
+    continuous-batching loop, each P(t) against the FP64 oracle at the FP32
+    bar at every step.  Jobs are drawn until the oracle's share of the test
+    would exceed about a minute of host time."""
+    import os
+
+    import oracle
+    from paper_0710_3747_gb300 import spinrp
+    spinrp.lib()
+    jobs = W.serve_stream(n=2000, seed=5, rate=1.0)
+    cand = [j for j in jobs if j.M <= 22]
+    rng = np.random.default_rng(7)
+    pick, cost = [], 0.0
+    for i in rng.permutation(len(cand)):
+        j = cand[i]
+        c = serve.job_work(j) / 1.0e10  # oracle seconds at about 1e10 updates/s
+        if cost + c > 60.0:
+            continue
+        pick.append(j)
+        cost += c
+        if len(pick) == 20:
+            break
+    assert len(pick) == 20
+    for j in pick:
+        j.arrival = 0.0
+    out = serve.run_stream(pick, "c64", max_active=8, chunk=20, realtime=False)
+    by_index = {j.meta["index"]: j for j in pick}
+    worst = 0.0
+    for r in out:
+        j = by_index[r.index]
+        Pw, _, _ = oracle.run(j.J, j.htype, j.seed, j.dt, j.steps, threads=os.cpu_count() or 1)
+        assert r.P.shape == Pw.shape
+        err = float(np.max(np.abs(r.P - Pw)))
+        worst = max(worst, err)
+        assert err <= 1e-4, (j.kind, j.M, j.steps, err)
+    print(f"20 sampled jobs (M {min(j.M for j in pick)}..{max(j.M for j in pick)}): max |dP| = {worst:.2e}")
