@@ -1312,6 +1312,7 @@ struct LaunchCtx {
 static size_t resident_bytes(const Plan &plan, const PassSet &ps, int prec, bool sites) {
   if (prec != SPINRP_C64 || !ps.phased || plan.segments() != 1 || plan.K != plan.M || sites) return 0;
   if (ps.only < 0 || ps.first < 0 || ps.midstep < 0 || ps.last < 0) return 0;
+  if (plan.M - ps.rb > 8) return 0;  // at most 256 threads per block
   const size_t b = (size_t(8) << plan.M) + sizeof(PhaseDesc) * ps.phases.size() +
                    sizeof(ROpRes) * ps.rops.size();
   return b <= kResidentMaxSmem ? b : 0;
