@@ -207,9 +207,13 @@ def run_reference(args, rank: int):
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_batch(args, rank: int, world: int, local_rank: int):
-    """Batched dipolar stars (M uniform in 12..22, dt 0.02): every job of the
-    batch evolved together, sweeps of each plan group as one launch, steady
-    steps replayed as one CUDA graph.  One bench step = init + all steps."""
+    """Batched dipolar stars (M uniform in 12..22, dt 0.02, `batch_steps`
+    Trotter steps): every job of the batch evolved together -- one-tile plans
+    (M <= 14) with the whole state resident in shared memory for all steps,
+    the others as one sweep launch per plan group with the steady steps
+    replayed as one CUDA graph.  One bench step = init + all Trotter steps of
+    every job.  Warm-up batches run 20 steps each (every kernel, graph and
+    plan exercised once)."""
     import torch
 
     from paper_0710_3747_gb300 import spinrp
@@ -218,43 +222,111 @@ def run_batch(args, rank: int, world: int, local_rank: int):
     torch.cuda.set_device(local_rank)
     spinrp.lib()
     jobs = W.star_batch(n=args.batch_jobs, seed=4 + rank, steps=args.batch_steps)
-    systems = [spinrp.System(j.J, j.htype) for j in jobs]
-    for s_ in systems:
-        if args.regbits:
-            s_.set_regbits(args.regbits)
-        if args.tile_K:
-            s_.set_tile("c64", min(args.tile_K, s_.M))
-    b = spinrp.Batch(systems, [j.seed for j in jobs], "c64", series_cap=args.batch_steps + 1)
-    upd = sum(updates_per_job(j.M, j.M * (j.M - 1) // 2, args.batch_steps) for j in jobs)
+    nsteps = args.batch_steps
 
-    def one():
-        b.init_random_phase()
-        b.evolve(0.02, args.batch_steps)
+    def make_systems():
+        out = []
+        for j in jobs:
+            s_ = spinrp.System(j.J, j.htype)
+            if args.regbits:
+                s_.set_regbits(args.regbits)
+            if args.tile_K:
+                s_.set_tile("c64", min(args.tile_K, s_.M))
+            out.append(s_)
+        return out
+
+    systems = make_systems()
+    b = spinrp.Batch(systems, [j.seed for j in jobs], "c64", series_cap=nsteps + 1)
+    upd = sum(updates_per_job(j.M, j.M * (j.M - 1) // 2, nsteps) for j in jobs)
+    # bytes the plan's sweeps move: per job and step, sweeps_per_step reads and
+    # writes of its state; a one-tile plan keeps the state in shared memory and
+    # moves it once per evolve call
+    plan_bytes = 0.0
+    for s_, j in zip(systems, jobs):
+        info = s_.plan_info("c64")
+        if info["K"] >= j.M:
+            plan_bytes += 16.0 * 2 ** j.M
+        else:
+            plan_bytes += 16.0 * 2 ** j.M * info["sweeps_per_step"] * nsteps
 
     for _ in range(args.warmup):
-        one()
+        b.init_random_phase()
+        b.evolve(0.02, min(nsteps, 20))
     torch.cuda.synchronize()
     n0 = spinrp.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(str(local_rank)) as clk:
         e0.record()
         for _ in range(args.steps):
-            one()
+            b.init_random_phase()
+            b.evolve(0.02, nsteps)
         e1.record()
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    launches = spinrp.launch_count() - n0
     mean, std = b.ensemble()
     info = b.info()
+    peaks, peak_src = _peaks()
+    achieved = plan_bytes / (ms / 1e3) / 1e9
     out = {"metric": METRIC, "value": world * upd / (ms / 1e3), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"star_batch_{args.batch_jobs}jobs_M12-22_dt0.02_{args.batch_steps}steps",
-                      "jobs": args.batch_jobs, "groups": info["groups"], "device_bytes": info["device_bytes"],
+           "config": {"workload": f"star_batch_{args.batch_jobs}jobs_M12-22_dt0.02_{nsteps}steps",
+                      "jobs": args.batch_jobs, "trotter_steps": nsteps, "groups": info["groups"],
+                      "device_bytes": info["device_bytes"],
+                      "l2": "states total far larger than L2; no flush",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
-           "gpu_launches": spinrp.launch_count() - n0, "clocks": clk.summary(),
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                        "kernel": "sweep2_kernel + resident_kernel (all sweep launches of the batch)",
+                        "algorithmic_bytes": "one read and one write of every state per planned sweep "
+                                             "(once per evolve call for states resident in shared memory)",
+                        "algorithmic_bytes_per_batch_job": plan_bytes,
+                        "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"},
+           "gpu_launches": launches, "clocks": clk.summary(),
            "ensemble": {"P_mean_end": float(mean[-1]), "P_spread_end": float(std[-1]),
                         "P_mean_t1": float(mean[len(mean) // 10]),
-                        "P_spread_t1": float(std[len(std) // 10])}}
+                        "P_spread_t1": float(std[len(std) // 10]),
+                        "chebyshev_scale_M12": 2.0 ** (-(12 - 1) / 2)}}
+    b.close()
+    # end to end through the public API: host couplings in, every job's P(t)
+    # and the ensemble out
+    if not args.skip_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sy = make_systems()
+        b2 = spinrp.Batch(sy, [j.seed for j in jobs], "c64", series_cap=nsteps + 1)
+        b2.init_random_phase().evolve(0.02, nsteps)
+        allP = [b2.polarization(k) for k in range(len(jobs))]
+        b2.ensemble()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        h2d = sum(j.J.nbytes for j in jobs) + 8 * len(jobs)
+        d2h = sum(p.nbytes for p in allP) + 2 * 8 * (nsteps + 1)
+        out["e2e"] = {"value": world * upd / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h), "s_per_step": e2e_s}
+        b2.close()
+    if rank == 0 and not args.skip_cpu:
+        # the oracle on a bounded sample: a few Trotter steps of three jobs
+        # (smallest, middle and largest M of the batch)
+        import oracle
+        threads = os.cpu_count() or 1
+        pick = sorted(range(len(jobs)), key=lambda k: jobs[k].M)
+        pick = [pick[0], pick[len(pick) // 2], pick[-1]]
+        done = 0.0
+        t_cpu = 0.0
+        for k in pick:
+            j = jobs[k]
+            a, bb = oracle.couplings(j.J, j.htype)
+            psi = oracle.init_random_phase(j.M, j.seed, threads=threads)
+            t0 = time.perf_counter()
+            oracle.evolve(psi, a, bb, j.dt, args.batch_cpu_steps, threads=threads)
+            t_cpu += time.perf_counter() - t0
+            done += updates_per_job(j.M, j.M * (j.M - 1) // 2, args.batch_cpu_steps)
+        out["cpu_baseline"] = {"value": done / t_cpu, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": (f"FP64 CPU oracle, {args.batch_cpu_steps} Trotter steps of 3 jobs of the "
+                                          f"batch (M = {', '.join(str(jobs[k].M) for k in pick)}), {threads} "
+                                          f"threads, {t_cpu:.1f} s")}
     if rank == 0:
         print(json.dumps(out))
     return 0
@@ -498,6 +570,7 @@ def main():
                     choices=["ladder_m30", "star_m20", "ladder_m14", "ladder_m26", "star_batch"])
     ap.add_argument("--batch-jobs", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=500)
+    ap.add_argument("--batch-cpu-steps", type=int, default=3, help="oracle steps per sampled job (star_batch)")
     ap.add_argument("--fp64-steps", type=int, default=-1,
                     help="Trotter steps of the complex128 run (default: all of the workload's)")
     ap.add_argument("--cpu-gates", type=int, default=43)

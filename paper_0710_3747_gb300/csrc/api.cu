@@ -69,7 +69,7 @@ struct spinrp_system {
   // one exists: mask of the first-colour spins (see Orientation)
   bool bipartite = false;
   uint64_t black = 0;
-  int orient_mode = 1;  // 1: complex64 states are oriented when they can be; 0: never
+  int orient_mode = 0;  // 1: complex64 states are oriented when they can be; 0: never
 };
 
 // Colour the spins of the flip-flop graph with two colours so that every bond

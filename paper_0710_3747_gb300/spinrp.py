@@ -224,8 +224,8 @@ class System:
         _check(lib().spinrp_system_set_regbits(self._h, int(rb)))
 
     def set_orientation(self, mode: int):
-        """1 (default): complex64 states of a bipartite system are stored
-        oriented (see include/spinrp.h); 0: always plainly."""
+        """1: complex64 states of a bipartite system are stored oriented (see
+        include/spinrp.h); 0 (default): always plainly."""
         _check(lib().spinrp_system_set_orientation(self._h, int(mode)))
 
     def plan_info(self, prec="c64") -> dict:

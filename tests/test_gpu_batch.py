@@ -69,22 +69,26 @@ def test_batch_spread_shrinks_with_m():
     assert spread[14] < spread[10] / 2.5
 
 
+@pytest.mark.slow
 def test_full_size_batch_sampled_jobs():
     """The bench's batch at its full size (4096 dipolar stars, M uniform in
-    12..22, the bench's seed and launch configuration) for 5 steps: sampled
-    jobs, including the largest, against the FP64 oracle at the FP32 bar; the
-    device ensemble mean equals the mean of the per-job series."""
+    12..22, the bench's seed and launch configuration) for 100 steps, the
+    steady steps replayed from graphs and the small stars resident in shared
+    memory: sampled jobs (the smallest and largest M and three others)
+    against the FP64 oracle at the FP32 bar at every step; the device
+    ensemble mean equals the mean of the per-job series."""
     spinrp.lib()
-    jobs = W.star_batch(n=4096, seed=4, steps=5)
+    steps = 100
+    jobs = W.star_batch(n=4096, seed=4, steps=steps)
     systems = [spinrp.System(j.J, j.htype) for j in jobs]
-    b = spinrp.Batch(systems, [j.seed for j in jobs], "c64", series_cap=6)
+    b = spinrp.Batch(systems, [j.seed for j in jobs], "c64", series_cap=steps + 1)
     assert b.info()["groups"] == 11
-    b.init_random_phase().evolve(0.02, 5)
+    b.init_random_phase().evolve(0.02, steps)
     Ms = np.array([j.M for j in jobs])
     picks = [0, 1777, 4095, int(np.argmax(Ms)), int(np.argmin(Ms))]
     for k in picks:
         j = jobs[k]
-        Pw, _, _ = oracle.run(j.J, j.htype, j.seed, 0.02, 5, threads=os.cpu_count() or 1)
+        Pw, _, _ = oracle.run(j.J, j.htype, j.seed, 0.02, steps, threads=os.cpu_count() or 1)
         assert np.max(np.abs(b.polarization(k) - Pw)) <= 1e-4, (k, j.M)
     mean, _ = b.ensemble()
     allP = np.array([b.polarization(k) for k in range(4096)])

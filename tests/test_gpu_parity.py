@@ -446,24 +446,26 @@ def _xy_ising_ladder(L):
 
 
 def test_orientation_is_used_where_it_applies():
-    """Ladders and chains (bipartite flip-flop graphs) get oriented complex64
-    states in the register-blocked kernel; stars, complex128 states and
-    systems set to plain storage do not."""
+    """With orientation requested, ladders and chains (bipartite flip-flop
+    graphs) get oriented complex64 states in the register-blocked kernel;
+    stars, complex128 states and systems left at the default (plain storage)
+    do not."""
     lad = spinrp.System(W.ladder(8, 1.0, 0.5), spinrp.XY)
     lad.set_tile("c64", 13)
+    assert spinrp.State(lad, "c64", series_cap=2).orientation() == 0  # default: plain
+    lad.set_orientation(1)
     st = spinrp.State(lad, "c64", series_cap=2)
     black = st.orientation()
     assert black != 0
-    # every bond joins the two colours
+    # every bond (1-based pairs) joins the two colours
     for i, j in lad.bonds():
-        assert ((black >> i) & 1) != ((black >> j) & 1)
+        assert ((black >> (i - 1)) & 1) != ((black >> (j - 1)) & 1)
     st.close()
     assert spinrp.State(lad, "c128", series_cap=2).orientation() == 0
     star = spinrp.System(W.star_dipolar(16, 8), spinrp.DIPOLAR)
     star.set_tile("c64", 13)
+    star.set_orientation(1)
     assert spinrp.State(star, "c64", series_cap=2).orientation() == 0
-    lad.set_orientation(0)
-    assert spinrp.State(lad, "c64", series_cap=2).orientation() == 0
 
 
 @pytest.mark.parametrize("rb,K", [(5, 11), (5, 12), (6, 12), (6, 13), (6, 14)])
@@ -508,6 +510,7 @@ def test_oriented_buffer_layout():
     J = W.ladder(7, 1.0, 0.5)
     s = spinrp.System(J, spinrp.XY)
     s.set_tile("c64", 12)
+    s.set_orientation(1)
     st = spinrp.State(s, "c64", series_cap=4)  # amplitude buffer from PyTorch
     st.init_random_phase(9).evolve(0.05, 3)
     black, lay = st.orientation(), st.layout()
