@@ -175,6 +175,12 @@ int spinrp_system_set_regbits(spinrp_system *sys, int rb);
  * Errors: SPINRP_EINVAL. */
 int spinrp_system_set_orientation(spinrp_system *sys, int mode);
 
+/* The storage orientation a state of precision prec created now would have:
+ * *black receives its mask of first-colour spins (bit q-1 = spin q), or 0 when
+ * it would be stored plainly.  Host only (plans the system).  Errors:
+ * SPINRP_EINVAL. */
+int spinrp_system_orientation(const spinrp_system *sys, int prec, uint64_t *black);
+
 /* Describe the sweep plan the library would use for precision prec: number
  * of segments the forward half step is cut into (*segments), device sweeps
  * per Trotter step in the steady state (*sweeps_per_step) and the tile width

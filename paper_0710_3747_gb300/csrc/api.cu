@@ -2126,6 +2126,18 @@ std::string audit_sweep2d(const PassDesc &d, const PhaseDesc *phases, int M, uin
 }
 }  // namespace
 
+extern "C" int spinrp_system_orientation(const spinrp_system *sys, int prec, uint64_t *black) {
+  if (!sys || !black || (prec != SPINRP_C64 && prec != SPINRP_C128))
+    return fail(SPINRP_EINVAL, "system_orientation: bad argument");
+  Plan plan;
+  PassSet ps;
+  int mb = 0;
+  const int rc = plan_state(*sys, prec, &plan, &ps, &mb);
+  if (rc) return rc;
+  *black = ps.oriented ? ps.black : 0;
+  return SPINRP_OK;
+}
+
 extern "C" int spinrp_system_plan_check(const spinrp_system *sys, int prec, double *phases_per_sweep,
                                         double *gates_per_phase) {
   if (!sys || (prec != SPINRP_C64 && prec != SPINRP_C128))

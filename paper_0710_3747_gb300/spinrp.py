@@ -70,6 +70,7 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             "spinrp_system_set_regbits": ([vp, ctypes.c_int], ctypes.c_int),
             "spinrp_system_set_orientation": ([vp, ctypes.c_int], ctypes.c_int),
             "spinrp_state_orientation": ([vp, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+            "spinrp_system_orientation": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
             "spinrp_system_plan_info": ([vp, ctypes.c_int, ip, ip, ip], ctypes.c_int),
             "spinrp_system_plan_gates": ([vp, ctypes.c_int, i32p, i32p, ctypes.c_int, ip], ctypes.c_int),
             "spinrp_state_bytes": ([vp, ctypes.c_int, ctypes.c_int64, szp, szp], ctypes.c_int),
@@ -227,6 +228,13 @@ class System:
         """1: complex64 states of a bipartite system are stored oriented (see
         include/spinrp.h); 0 (default): always plainly."""
         _check(lib().spinrp_system_set_orientation(self._h, int(mode)))
+
+    def orientation(self, prec="c64") -> int:
+        """First-colour mask a state of this precision would be oriented with
+        (0: stored plainly); host only."""
+        m = ctypes.c_uint64()
+        _check(lib().spinrp_system_orientation(self._h, _PREC[prec], ctypes.byref(m)))
+        return int(m.value)
 
     def plan_info(self, prec="c64") -> dict:
         s, w, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

@@ -357,3 +357,47 @@ def test_constructors_reject_bad_arguments():
                  lambda: spinrp.System.star_dipolar(8, 1, rmin=0.9)):
         with pytest.raises(spinrp.SpinrpError):
             call()
+
+
+@pytest.mark.parametrize("name,J,htype,a,K,rb", [
+    ("ladder30_K13", W.ladder(15, 1.0, 0.5), W.XY, None, 13, 6),
+    ("ladder16_K12", W.ladder(8, 1.0, 0.5), W.XY, None, 12, 5),
+    ("ladder16_K14", W.ladder(8, 1.0, 0.5), W.XY, None, 14, 6),
+    ("ladder12_one_tile", W.ladder(6, 1.0, 0.3), W.XY, None, 12, 6),
+    ("chain19_K11", W.chain(19, 0.8), W.XY, None, 11, 5),
+    ("xy_ising_ladder16", W.ladder(8, 1.0, 0.6), W.GENERIC, 0.4 * W.ladder(8, 1.0, 1.0), 13, 6),
+])
+def test_oriented_register_programs(name, J, htype, a, K, rb):
+    """Oriented programs (bipartite couplings, orientation requested): every
+    phase holds its first-colour register bits first in an allowed count,
+    every gate joins the two colours, and the packed arithmetic of the
+    oriented kernel -- emulated in FP64 thread by thread and word by word,
+    (Re, Im) / (Im, Re) words, sign pattern and conjugated diagonal phases --
+    reproduces the plain program on a random tile for both orientations of
+    the outer bits (spinrp_system_plan_check)."""
+    s = spinrp.System(J, htype, a)
+    s.set_tile("c64", K)
+    s.set_regbits(rb)
+    s.set_orientation(1)
+    black = s.orientation("c64")
+    assert black != 0
+    for i, j in s.bonds():  # 1-based pairs: every bond joins the two colours
+        assert ((black >> (i - 1)) & 1) != ((black >> (j - 1)) & 1)
+    assert s.orientation("c128") == 0
+    r = s.plan_check("c64")
+    assert r["phases_per_sweep"] > 0
+    # the same system with plain storage plans the same number of phases
+    s.set_orientation(0)
+    assert abs(s.plan_check("c64")["phases_per_sweep"] - r["phases_per_sweep"]) < 1.0
+
+
+def test_orientation_setting_is_validated():
+    s = spinrp.System(W.ladder(7), W.XY)
+    with pytest.raises(spinrp.SpinrpError):
+        s.set_orientation(2)
+    assert s.orientation() == 0  # default: plain storage
+    s.set_orientation(1)
+    assert s.orientation() != 0
+    star = spinrp.System(W.star_dipolar(14, 2), W.DIPOLAR)
+    star.set_orientation(1)
+    assert star.orientation() == 0  # not bipartite
