@@ -18,6 +18,7 @@
 #include "../../include/spinrp.h"
 #include "internal.h"
 #include "kernels.cuh"
+#include "persist.cuh"
 #include "sectors.cuh"
 #include "sweep2d.cuh"
 
@@ -2278,10 +2279,21 @@ struct spinrp_batch {
   size_t bytes = 0;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graphs[2] = {nullptr, nullptr};
+  // one persistent launch for the multi-tile groups (persist.cuh)
+  bool persist = true;
+  int persist_K = 0;                   // common tile width of the eligible groups (0: none)
+  unsigned char *d_persist = nullptr;  // PersistPlan, queue, error word, per-job counters
+  PersistPlan *h_plan = nullptr;       // host copy of the uploaded plan
+  int64_t plan_steps = -1;             // steps the uploaded plan and its graph are for
+  cudaGraphExec_t pgraph = nullptr;
+  unsigned persist_blocks = 0;
 };
 
 static void free_batch(spinrp_batch *b) {
   if (!b) return;
+  if (b->pgraph) cudaGraphExecDestroy(b->pgraph);
+  if (b->d_persist) cudaFree(b->d_persist);
+  delete b->h_plan;
   for (cudaGraphExec_t g : b->graphs)
     if (g) cudaGraphExecDestroy(g);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -2289,6 +2301,85 @@ static void free_batch(spinrp_batch *b) {
     if (g.dev) cudaFree(g.dev);
   if (b->dev_common) cudaFree(b->dev_common);
   delete b;
+}
+
+// A multi-tile group can join the persistent launch: complex64 register
+// programs of six register bits on 13- or 14-spin tiles (the launch's block
+// size), plain storage, at most 31 outer bits, a step's sweeps in the plan's
+// steady list.
+static bool persist_eligible(const BatchGroup &g, int prec) {
+  return prec == SPINRP_C64 && !g.ctx.resident && g.ps.phased && !g.ps.oriented && g.ps.rb == 6 &&
+         (g.plan.K == 13 || g.plan.K == 14) && g.plan.M - g.plan.K <= 31 && g.plan.segments() >= 2 &&
+         g.plan.sweeps_per_step() - 1 <= kMaxSteadyPasses && g.ps.head >= 0 && g.ps.join >= 0 &&
+         g.ps.tail >= 0 && g.ps.mid >= 0;
+}
+
+static bool in_persist(const spinrp_batch *b, const BatchGroup &g) {
+  return b->persist && b->persist_K > 0 && persist_eligible(g, b->prec) && g.plan.K == b->persist_K;
+}
+
+// The host plan of a persistent launch of `steps` Trotter steps over the
+// batch's groups in the launch; false if the counts do not fit.
+static bool build_persist_plan(const spinrp_batch *b, int64_t steps, PersistPlan *pp) {
+  memset(pp, 0, sizeof *pp);
+  std::vector<const BatchGroup *> gs;
+  for (const BatchGroup &g : b->groups)
+    if (in_persist(b, g)) gs.push_back(&g);
+  if (gs.empty() || gs.size() > (size_t)kMaxPersistGroups) return false;
+  std::stable_sort(gs.begin(), gs.end(), [](const BatchGroup *x, const BatchGroup *y) {
+    return x->plan.sweeps_per_step() > y->plan.sweeps_per_step();
+  });
+  pp->ngroups = (int)gs.size();
+  pp->steps = steps;
+  int done0 = 0;
+  unsigned long long cum = 0;
+  for (int i = 0; i < pp->ngroups; ++i) {
+    const BatchGroup &g = *gs[i];
+    PersistGroup &G = pp->g[i];
+    G.M = g.M;
+    G.K = g.plan.K;
+    G.njobs = (int)g.jobs.size();
+    G.done0 = done0;
+    done0 += G.njobs;
+    G.S = g.plan.sweeps_per_step();
+    const int64_t nsw = 1 + (int64_t)G.S * steps;
+    G.tiles = 1u << (g.M - g.plan.K);
+    if (nsw > (int64_t)1 << 30 || (uint64_t)nsw * G.tiles >= (uint64_t)1 << 32) return false;
+    G.nsweeps = (int)nsw;
+    G.head = g.ps.head;
+    G.join = g.ps.join;
+    G.tail = g.ps.tail;
+    int q = 0;
+    for (int id : g.ps.body) G.steady[q++] = id;
+    G.steady[q++] = g.ps.mid;
+    for (int id : g.ps.bodyr) G.steady[q++] = id;
+    if (q != G.S - 1) return false;
+    G.cum = cum;
+    cum += (unsigned long long)G.njobs * G.tiles;
+    G.passes = g.ctx.passes;
+    G.phases = g.ctx.phases;
+    G.jobs = g.ctx.jobs;
+  }
+  // regions of sweep indices with a fixed set of active groups (groups sorted
+  // by sweeps per step, so by sweep count, most first)
+  int nreg = 0;
+  unsigned long long item = 0;
+  int from = 0;
+  for (int a = pp->ngroups; a >= 1; --a) {
+    const int to = pp->g[a - 1].nsweeps;  // groups 0..a-1 are active below `to`
+    if (to <= from) continue;
+    pp->start[nreg] = from;
+    pp->active[nreg] = a;
+    pp->base[nreg] = item;
+    pp->per[nreg] = pp->g[a - 1].cum + (unsigned long long)pp->g[a - 1].njobs * pp->g[a - 1].tiles;
+    item += pp->per[nreg] * (unsigned long long)(to - from);
+    from = to;
+    ++nreg;
+  }
+  pp->start[nreg] = from;
+  pp->nregions = nreg;
+  pp->total = item;
+  return nreg > 0;
 }
 
 extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *systems,
@@ -2453,6 +2544,34 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
   }
   for (BatchGroup &g : b->groups)
     if (g.ps.phased) g.ctx.prefetch_ahead = sweep2_resident(prec, g.ps.rb, g.plan.K, g.ps.oriented);
+  // the persistent launch takes the eligible groups of the most common
+  // eligible tile width (jobs counted)
+  {
+    int n13 = 0, n14 = 0;
+    for (const BatchGroup &g : b->groups)
+      if (persist_eligible(g, prec)) (g.plan.K == 13 ? n13 : n14) += (int)g.jobs.size();
+    b->persist_K = n13 + n14 == 0 ? 0 : (n13 >= n14 ? 13 : 14);
+  }
+  if (b->persist_K) {
+    const size_t bytes = align256(sizeof(PersistPlan)) + 256 + sizeof(unsigned) * (size_t)njobs;
+    cudaError_t e2 = cudaMalloc((void **)&b->d_persist, bytes);
+    b->h_plan = new (std::nothrow) PersistPlan;
+    int per = 0, dev = 0, sms = 0;
+    const int smem = 8 << b->persist_K;
+    if (e2 == cudaSuccess)
+      e2 = cudaFuncSetAttribute(persist_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e2 == cudaSuccess) e2 = cudaGetDevice(&dev);
+    if (e2 == cudaSuccess) e2 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e2 == cudaSuccess)
+      e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, persist_kernel<6>, 1 << (b->persist_K - 6), smem);
+    if (e2 != cudaSuccess || !b->h_plan || per < 1) {
+      cudaGetLastError();
+      free_batch(b);
+      return fail(SPINRP_ENOMEM, "batch_create: persistent launch setup failed");
+    }
+    b->persist_blocks = (unsigned)(per * sms);
+    b->bytes += bytes;
+  }
   *out = b;
   return SPINRP_OK;
 }
@@ -2498,6 +2617,73 @@ extern "C" int spinrp_batch_init_random_phase(spinrp_batch *b) { return batch_in
 
 extern "C" int spinrp_batch_init_product_phase(spinrp_batch *b) { return batch_init(b, INIT_PRODUCT); }
 
+// Device layout of b->d_persist: the plan, then (at +align256(plan)) the
+// queue counter (8 bytes), the error word (at +64) and the per-job counters
+// (at +256).
+static unsigned long long *persist_queue(spinrp_batch *b) {
+  return (unsigned long long *)(b->d_persist + align256(sizeof(PersistPlan)));
+}
+static int *persist_err(spinrp_batch *b) { return (int *)((unsigned char *)persist_queue(b) + 64); }
+static unsigned *persist_done(spinrp_batch *b) { return (unsigned *)((unsigned char *)persist_queue(b) + 256); }
+
+// The multi-tile groups' `steps` Trotter steps as one persistent launch,
+// replayed from a CUDA graph (counters cleared, then the launch) captured for
+// this step count.
+static int persist_evolve(spinrp_batch *b, int64_t steps) {
+  int njobs = 0;
+  for (const BatchGroup &g : b->groups)
+    if (in_persist(b, g)) njobs += (int)g.jobs.size();
+  if (b->plan_steps != steps) {
+    if (!build_persist_plan(b, steps, b->h_plan))
+      return fail(SPINRP_EUNSUPPORTED, "batch_evolve: persistent plan does not fit (%lld steps)", (long long)steps);
+    CUDA_TRY(cudaMemcpyAsync(b->d_persist, b->h_plan, sizeof(PersistPlan), cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    if (b->pgraph) cudaGraphExecDestroy(b->pgraph), b->pgraph = nullptr;
+    b->plan_steps = steps;
+  }
+  if (!b->pgraph) {
+    if (!b->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaMemsetAsync(persist_queue(b), 0, 256 + sizeof(unsigned) * (size_t)njobs, b->cap_stream);
+    const unsigned nt = 1u << (b->persist_K - 6);
+    persist_kernel<6><<<b->persist_blocks, nt, size_t(8) << b->persist_K, b->cap_stream>>>(
+        (const PersistPlan *)b->d_persist, persist_queue(b), persist_done(b), persist_err(b), b->persist_blocks);
+    cudaGraph_t gr = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &gr);
+    if (e != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      cudaGetLastError();
+      return fail(SPINRP_ECUDA, "batch_evolve: persistent graph capture: %s", cudaGetErrorString(e));
+    }
+    const cudaError_t e2 = cudaGraphInstantiate(&b->pgraph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e2 != cudaSuccess) {
+      b->pgraph = nullptr;
+      return fail(SPINRP_ECUDA, "batch_evolve: persistent graph instantiate: %s", cudaGetErrorString(e2));
+    }
+  }
+  CUDA_TRY(cudaGraphLaunch(b->pgraph, b->stream));
+  ++g_launches;
+  return SPINRP_OK;
+}
+
+// SPINRP_ETIMEOUT when a wait of the last persistent launch gave up
+// (synchronizes the batch's stream).
+static int persist_check(spinrp_batch *b) {
+  if (!b->d_persist || b->plan_steps < 0) return SPINRP_OK;
+  int err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err, persist_err(b), sizeof err, cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  if (err) return fail(SPINRP_ETIMEOUT, "batch: a persistent-launch wait timed out; the series are invalid");
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_batch_set_persistent(spinrp_batch *b, int on) {
+  if (!b || (on != 0 && on != 1)) return fail(SPINRP_EINVAL, "batch_set_persistent: bad argument");
+  b->persist = on != 0;
+  return SPINRP_OK;
+}
+
 extern "C" int spinrp_batch_evolve(spinrp_batch *b, double dt, int64_t steps, int order) {
   if (!b) return fail(SPINRP_EINVAL, "batch_evolve: batch is NULL");
   if (order != 2) return fail(SPINRP_EUNSUPPORTED, "batch_evolve: only order 2 is implemented");
@@ -2530,11 +2716,21 @@ extern "C" int spinrp_batch_evolve(spinrp_batch *b, double dt, int64_t steps, in
     b->coef_dt = dt;
   }
   std::vector<LaunchCtx> cs;
-  for (BatchGroup &g : b->groups) cs.push_back(g.ctx);
-  const int rc = b->prec == SPINRP_C64
-                     ? run_steps<float>(cs, b->stream, steps, true, &b->cap_stream, b->graphs)
-                     : run_steps<double>(cs, b->stream, steps, true, &b->cap_stream, b->graphs);
-  if (rc) return rc;
+  bool any_persist = false;
+  for (BatchGroup &g : b->groups) {
+    if (in_persist(b, g)) any_persist = true;
+    else cs.push_back(g.ctx);
+  }
+  if (!cs.empty()) {
+    const int rc = b->prec == SPINRP_C64
+                       ? run_steps<float>(cs, b->stream, steps, true, &b->cap_stream, b->graphs)
+                       : run_steps<double>(cs, b->stream, steps, true, &b->cap_stream, b->graphs);
+    if (rc) return rc;
+  }
+  if (any_persist) {
+    const int rc = persist_evolve(b, steps);
+    if (rc) return rc;
+  }
   b->len += steps;
   return SPINRP_OK;
 }
@@ -2545,6 +2741,7 @@ extern "C" int spinrp_batch_polarization(spinrp_batch *b, int job, double *out, 
   *n = b->len;
   const int64_t m = std::min(cap, b->len);
   if (m <= 0) return SPINRP_OK;
+  if (int rc = persist_check(b)) return rc;
   std::vector<double> buf(2 * m);
   CUDA_TRY(cudaMemcpyAsync(buf.data(), b->hjobs[job].series, sizeof(double) * 2 * m,
                            cudaMemcpyDeviceToHost, b->stream));
@@ -2559,6 +2756,7 @@ extern "C" int spinrp_batch_ensemble(spinrp_batch *b, double *mean, double *stdd
   *n = b->len;
   const int64_t len = b->len, m = std::min(cap, len);
   if (len <= 0 || m <= 0) return SPINRP_OK;
+  if (int rc = persist_check(b)) return rc;
   ++g_launches;
   ensemble_kernel<<<(unsigned)((len + 127) / 128), 128, 0, b->stream>>>(b->d_all, (int)b->hjobs.size(),
                                                                           len, b->d_ens);

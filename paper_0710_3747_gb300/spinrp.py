@@ -499,6 +499,7 @@ _BATCH_SIG = {
     "spinrp_batch_init_random_phase": ([ctypes.c_void_p], ctypes.c_int),
     "spinrp_batch_init_product_phase": ([ctypes.c_void_p], ctypes.c_int),
     "spinrp_batch_evolve": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
+    "spinrp_batch_set_persistent": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "spinrp_batch_polarization": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                    ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "spinrp_batch_ensemble": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -541,6 +542,12 @@ class Batch:
         bts, g = ctypes.c_size_t(), ctypes.c_int()
         _check(_batch_lib().spinrp_batch_info(self._h, ctypes.byref(bts), ctypes.byref(g)))
         return {"device_bytes": bts.value, "groups": g.value}
+
+    def set_persistent(self, on: bool = True):
+        """Multi-tile groups in one persistent launch per evolve (default) or
+        one launch per sweep."""
+        _check(_batch_lib().spinrp_batch_set_persistent(self._h, int(bool(on))))
+        return self
 
     def init_random_phase(self):
         _check(_batch_lib().spinrp_batch_init_random_phase(self._h))
