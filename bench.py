@@ -237,6 +237,7 @@ def run_batch(args, rank: int, world: int, local_rank: int):
 
     systems = make_systems()
     b = spinrp.Batch(systems, [j.seed for j in jobs], "c64", series_cap=nsteps + 1)
+    b.set_persistent(args.batch_launch == "persistent")
     upd = sum(updates_per_job(j.M, j.M * (j.M - 1) // 2, nsteps) for j in jobs)
     # bytes the plan's sweeps move: per job and step, sweeps_per_step reads and
     # writes of its state; a one-tile plan keeps the state in shared memory and
@@ -273,6 +274,7 @@ def run_batch(args, rank: int, world: int, local_rank: int):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"star_batch_{args.batch_jobs}jobs_M12-22_dt0.02_{nsteps}steps",
                       "jobs": args.batch_jobs, "trotter_steps": nsteps, "groups": info["groups"],
+                      "launch": args.batch_launch,
                       "device_bytes": info["device_bytes"],
                       "l2": "states total far larger than L2; no flush",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -296,6 +298,7 @@ def run_batch(args, rank: int, world: int, local_rank: int):
         t0 = time.perf_counter()
         sy = make_systems()
         b2 = spinrp.Batch(sy, [j.seed for j in jobs], "c64", series_cap=nsteps + 1)
+        b2.set_persistent(args.batch_launch == "persistent")
         b2.init_random_phase().evolve(0.02, nsteps)
         allP = [b2.polarization(k) for k in range(len(jobs))]
         b2.ensemble()
@@ -571,6 +574,8 @@ def main():
     ap.add_argument("--batch-jobs", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--batch-cpu-steps", type=int, default=3, help="oracle steps per sampled job (star_batch)")
+    ap.add_argument("--batch-launch", choices=["persistent", "per-sweep"], default="persistent",
+                    help="star_batch: multi-tile groups in one persistent launch, or one launch per sweep")
     ap.add_argument("--fp64-steps", type=int, default=-1,
                     help="Trotter steps of the complex128 run (default: all of the workload's)")
     ap.add_argument("--cpu-gates", type=int, default=43)
