@@ -236,6 +236,20 @@ def run_batch(args, rank: int, world: int, local_rank: int):
         return out
 
     systems = make_systems()
+    tuned = None
+    if args.autotune:
+        tuned = spinrp.autotune_batch(systems, [j.seed for j in jobs])
+        args.tile_K, args.regbits = 0, 0  # make_systems() below repeats the tuned setting by hand
+
+        def make_systems():
+            out = []
+            for j in jobs:
+                s_ = spinrp.System(j.J, j.htype)
+                if s_.M >= 15:
+                    s_.set_tile("c64", tuned["K"])
+                    s_.set_regbits(6)
+                out.append(s_)
+            return out
     b = spinrp.Batch(systems, [j.seed for j in jobs], "c64", series_cap=nsteps + 1)
     b.set_persistent(args.batch_launch == "persistent")
     upd = sum(updates_per_job(j.M, j.M * (j.M - 1) // 2, nsteps) for j in jobs)
@@ -275,6 +289,8 @@ def run_batch(args, rank: int, world: int, local_rank: int):
            "config": {"workload": f"star_batch_{args.batch_jobs}jobs_M12-22_dt0.02_{nsteps}steps",
                       "jobs": args.batch_jobs, "trotter_steps": nsteps, "groups": info["groups"],
                       "launch": args.batch_launch,
+                      "autotuned": None if tuned is None else {"K": tuned["K"],
+                                                               "ms_per_step": {str(k): v for k, v in tuned["ms_per_step"].items()}},
                       "device_bytes": info["device_bytes"],
                       "l2": "states total far larger than L2; no flush",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -459,6 +475,24 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "sweep_bandwidth_gbs": kernel_bw, "sweep_bandwidth_frac": kernel_bw / peaks["hbm_gbs"],
                 "sweep_share_of_job": sweep_ms / (ms_prof * args.steps),
                 "timing": "per-launch CUDA events in a second pass over the same jobs (live launches)"}
+    # a state that fits in L2 (129 MB) never streams from HBM: its sweeps are
+    # bound inside the SMs, so the roofline is the gate arithmetic's FP32 rate
+    # (each gate rotates 2^M / 4 flip-flop pairs at 6 FMAs: 1.5 FMA = 3 FLOP
+    # per amplitude update) against the FP32 peak derived from the unit count
+    # and the maximum SM clock (128 FP32 FMA lanes per SM), not HBM
+    if state_bytes < 126 * 2 ** 20 and prec == "c64":
+        sms = torch.cuda.get_device_properties(stream.device).multi_processor_count
+        peak32 = sms * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 * 128 * 2 / 1e12
+        flop_launch = 3.0 * updates_per_job(job.M, nb, job.steps) / max(sweep_n / args.steps, 1)
+        ach32 = flop_launch / sweep_avg_s / 1e12
+        roofline = {"bound": "alu", "achieved": ach32, "peak": peak32, "unit": "TFLOP/s",
+                    "frac": ach32 / peak32, "traffic": None, "kernel": roofline["kernel"],
+                    "peak_source": "derived: SMs x max SM clock x 128 FP32 FMA lanes x 2 FLOP",
+                    "flops": "flip-flop gate FMAs of the launch (the step's gate applications / sweeps)",
+                    "launches": sweep_n, "mean_launch_ms": sweep_avg_s * 1e3,
+                    "l2_resident": True, "hbm_frac_if_streamed": roofline["frac"],
+                    "sweep_share_of_job": roofline["sweep_share_of_job"],
+                    "timing": roofline["timing"]}
     # the same fraction over whole jobs (graph replays, init included)
     min_bytes_step = min_sweeps * sweep_bytes
     step_roof = {"min_sweeps_per_step": min_sweeps, "sweeps_per_step": info["sweeps_per_step"],

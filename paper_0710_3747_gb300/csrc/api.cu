@@ -2345,6 +2345,7 @@ static bool build_persist_plan(const spinrp_batch *b, int64_t steps, PersistPlan
     const int64_t nsw = 1 + (int64_t)G.S * steps;
     G.tiles = 1u << (g.M - g.plan.K);
     if (nsw > (int64_t)1 << 30 || (uint64_t)nsw * G.tiles >= (uint64_t)1 << 32) return false;
+    if ((uint64_t)G.njobs * G.tiles >= (uint64_t)1 << 31) return false;
     G.nsweeps = (int)nsw;
     G.head = g.ps.head;
     G.join = g.ps.join;
@@ -2372,6 +2373,7 @@ static bool build_persist_plan(const spinrp_batch *b, int64_t steps, PersistPlan
     pp->active[nreg] = a;
     pp->base[nreg] = item;
     pp->per[nreg] = pp->g[a - 1].cum + (unsigned long long)pp->g[a - 1].njobs * pp->g[a - 1].tiles;
+    if (pp->per[nreg] >= (1ull << 32)) return false;  // items per sweep index fit 32 bits
     item += pp->per[nreg] * (unsigned long long)(to - from);
     from = to;
     ++nreg;

@@ -188,46 +188,67 @@ persist_kernel(const PersistPlan *__restrict__ plan, unsigned long long *queue, 
   __shared__ int s_go, s_last;
   const int tid = threadIdx.x, nt = blockDim.x;
   const unsigned long long total = plan->total;
-  for (;;) {
-    if (tid == 0) s_item = atomicAdd(queue, 1ull);
-    __syncthreads();
-    const unsigned long long x = s_item;
-    if (x >= total) break;
-    // decode the item: region, sweep index, group, job, tile
+  // thread 0 decodes an item into (sweep index, group, job, pass, tile); the
+  // next item is taken from the queue while the current one computes
+  struct Item {
+    int i, gi, jl, pass;
+    unsigned r;
+  };
+  __shared__ Item s_it;
+  auto decode = [&](unsigned long long x) -> Item {
+    Item it;
     int k = 0;
     while (k + 1 < plan->nregions && x >= plan->base[k + 1]) ++k;
     const unsigned long long off = x - plan->base[k];
-    const int i = plan->start[k] + (int)(off / plan->per[k]);
-    const unsigned long long rem = off % plan->per[k];
+    const unsigned per = (unsigned)plan->per[k];  // < 2^32 (host check)
+    const unsigned long long q0 = off / per;
+    it.i = plan->start[k] + (int)q0;
+    const unsigned rem = (unsigned)(off - q0 * per);
     int gi = 0;
     while (gi + 1 < plan->active[k] && rem >= plan->g[gi + 1].cum) ++gi;
     const PersistGroup &G = plan->g[gi];
-    const unsigned long long w = rem - G.cum;
-    const int jl = (int)(w / G.tiles);
-    const unsigned r = (unsigned)(w % G.tiles);
-    int pass;
-    if (i == 0) {
-      pass = G.head;
+    const unsigned w = rem - (unsigned)G.cum;
+    it.gi = gi;
+    it.jl = (int)(w / G.tiles);
+    it.r = w - (unsigned)it.jl * G.tiles;
+    if (it.i == 0) {
+      it.pass = G.head;
     } else {
-      const int q = (i - 1) % G.S;
-      const long long step = (i - 1) / G.S;
-      pass = q < G.S - 1 ? G.steady[q] : (step == plan->steps - 1 ? G.tail : G.join);
+      const int q = (it.i - 1) % G.S;
+      const long long step = (it.i - 1) / G.S;
+      it.pass = q < G.S - 1 ? G.steady[q] : (step == plan->steps - 1 ? G.tail : G.join);
     }
-    // the job's earlier sweeps, every tile of them, must be done
+    return it;
+  };
+  unsigned long long next = 0;
+  if (tid == 0) next = atomicAdd(queue, 1ull);
+  for (;;) {
     if (tid == 0) {
-      const unsigned need = (unsigned)i * G.tiles;
-      int ok = 1;
-      unsigned polls = 0;
-      while (pq::ld_acquire(done + G.done0 + jl) < need) {
-        if (++polls > kPersistWaitLimit || pq::ld_relaxed(err)) {
-          ok = 0;
-          break;
+      s_item = next;
+      s_go = next < total;
+      if (s_go) {
+        const Item it = decode(next);
+        s_it = it;
+        // the job's earlier sweeps, every tile of them, must be done
+        const PersistGroup &G = plan->g[it.gi];
+        const unsigned need = (unsigned)it.i * G.tiles;
+        unsigned polls = 0;
+        while (pq::ld_acquire(done + G.done0 + it.jl) < need) {
+          if (++polls > kPersistWaitLimit || pq::ld_relaxed(err)) {
+            atomicExch(err, 1);
+            s_go = 0;
+            break;
+          }
+          __nanosleep(100);
         }
-        __nanosleep(100);
       }
-      if (!ok) atomicExch(err, 1);
-      s_go = ok;
     }
+    __syncthreads();
+    if (!s_go) break;
+    const Item it = s_it;
+    const PersistGroup &G = plan->g[it.gi];
+    const int jl = it.jl, pass = it.pass;
+    const unsigned r = it.r;
     // the pass descriptor
     {
       const int nwords = (int)(sizeof(PassDesc) / 4);
@@ -235,7 +256,6 @@ persist_kernel(const PersistPlan *__restrict__ plan, unsigned long long *queue, 
       for (int q = tid; q < nwords; q += nt) reinterpret_cast<int *>(&s_d)[q] = src[q];
     }
     __syncthreads();
-    if (!s_go) break;
     const PassDesc &d = s_d;
     const JobPtrs jp = G.jobs[jl];
     float2 *__restrict__ psi = static_cast<float2 *>(jp.psi);
@@ -254,6 +274,7 @@ persist_kernel(const PersistPlan *__restrict__ plan, unsigned long long *queue, 
     // job's same sweep
     if (ahead && r + ahead < G.tiles) sw2::prefetch_tile<RB>(psi, sw2::tile_origin(r + ahead, d, M), d, tid, lognt);
     pq::load_tile_cg<RB>(psi, base, d, tid, lognt, tile2);
+    if (tid == 0) next = atomicAdd(queue, 1ull);
     sw2::cp_async_wait_all();
     __syncthreads();
     float up = 0.f, dn = 0.f;

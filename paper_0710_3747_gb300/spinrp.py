@@ -585,3 +585,38 @@ class Batch:
 
     def __del__(self):
         self.close()
+
+
+def autotune_batch(systems: list, seeds, candidates=(13, 14), probe_steps: int = 20, dt: float = 0.02,
+                   min_M: int = 15, repeats: int = 1) -> dict:
+    """Pick the common tile width of a batch's multi-tile groups (systems of
+    at least min_M spins, six register bits: the persistent launch's tiles)
+    by timing `probe_steps` Trotter steps of the whole batch per candidate on
+    the device (CUDA events, after a warm-up call of the same length that
+    also plans and captures), then set the winner on those systems.  Returns
+    {"K": best K, "ms_per_step": {K: ms}}."""
+    import torch
+    big = [s for s in systems if s.M >= min_M]
+    timings = {}
+    for K in candidates:
+        for s in big:
+            s.set_tile(C64, min(K, s.M))
+            s.set_regbits(6)
+        b = Batch(systems, seeds, "c64", series_cap=1 + (repeats + 1) * probe_steps)
+        b.init_random_phase().evolve(dt, probe_steps)
+        best = float("inf")
+        for _ in range(repeats):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.evolve(dt, probe_steps)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / probe_steps)
+        timings[K] = best
+        b.close()
+    K_best = min(timings, key=timings.get)
+    for s in big:
+        s.set_tile(C64, min(K_best, s.M))
+        s.set_regbits(6)
+    return {"K": K_best, "ms_per_step": timings}
+
