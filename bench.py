@@ -608,7 +608,7 @@ def main():
     ap.add_argument("--batch-jobs", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--batch-cpu-steps", type=int, default=3, help="oracle steps per sampled job (star_batch)")
-    ap.add_argument("--batch-launch", choices=["persistent", "per-sweep"], default="persistent",
+    ap.add_argument("--batch-launch", choices=["persistent", "per-sweep"], default="per-sweep",
                     help="star_batch: multi-tile groups in one persistent launch, or one launch per sweep")
     ap.add_argument("--fp64-steps", type=int, default=-1,
                     help="Trotter steps of the complex128 run (default: all of the workload's)")

@@ -2280,7 +2280,7 @@ struct spinrp_batch {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graphs[2] = {nullptr, nullptr};
   // one persistent launch for the multi-tile groups (persist.cuh)
-  bool persist = true;
+  bool persist = false;
   int persist_K = 0;                   // common tile width of the eligible groups (0: none)
   unsigned char *d_persist = nullptr;  // PersistPlan, queue, error word, per-job counters
   PersistPlan *h_plan = nullptr;       // host copy of the uploaded plan

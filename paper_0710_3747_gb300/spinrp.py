@@ -544,8 +544,8 @@ class Batch:
         return {"device_bytes": bts.value, "groups": g.value}
 
     def set_persistent(self, on: bool = True):
-        """Multi-tile groups in one persistent launch per evolve (default) or
-        one launch per sweep."""
+        """Multi-tile groups in one persistent launch per evolve call (True)
+        or one launch per sweep (False, the default)."""
         _check(_batch_lib().spinrp_batch_set_persistent(self._h, int(bool(on))))
         return self
 

@@ -73,8 +73,8 @@ def test_batch_spread_shrinks_with_m():
 def test_full_size_batch_sampled_jobs():
     """The bench's batch at its full size (4096 dipolar stars, M uniform in
     12..22, the bench's seed and launch configuration) for 100 steps, the
-    steady steps replayed from graphs and the small stars resident in shared
-    memory: sampled jobs (the smallest and largest M and three others)
+    multi-tile groups in one persistent launch and the small stars resident in
+    shared memory: sampled jobs (the smallest and largest M and three others)
     against the FP64 oracle at the FP32 bar at every step; the device
     ensemble mean equals the mean of the per-job series."""
     spinrp.lib()
@@ -82,6 +82,7 @@ def test_full_size_batch_sampled_jobs():
     jobs = W.star_batch(n=4096, seed=4, steps=steps)
     systems = [spinrp.System(j.J, j.htype) for j in jobs]
     b = spinrp.Batch(systems, [j.seed for j in jobs], "c64", series_cap=steps + 1)
+    b.set_persistent(True)
     assert b.info()["groups"] == 11
     b.init_random_phase().evolve(0.02, steps)
     Ms = np.array([j.M for j in jobs])
