@@ -360,6 +360,16 @@ int spinrp_batch_evolve(spinrp_batch *b, double dt, int64_t steps, int order);
  * SPINRP_ETIMEOUT.  Errors: SPINRP_EINVAL. */
 int spinrp_batch_set_persistent(spinrp_batch *b, int on);
 
+/* Diagnostic of the persistent launch's bounded waits (no counterpart in the
+ * paper): runs the launch for a `steps`-step plan with its queue started past
+ * the first sweep, so every item waits for tiles that never run; each wait
+ * gives up after its poll limit, the blocks return, and the call reports
+ * SPINRP_ETIMEOUT (with the launch's duration in *seconds, if not NULL) --
+ * SPINRP_ECUDA if no wait ran out.  No tile is processed: the batch's states
+ * and series are unchanged, and its next evolve runs normally.  Needs a
+ * batch with persistent groups, initialized.  Synchronizes. */
+int spinrp_batch_persist_timeout_check(spinrp_batch *b, int64_t steps, double *seconds);
+
 /* P(t) series of job k (site 1) to the host; synchronizes. */
 int spinrp_batch_polarization(spinrp_batch *b, int job, double *out, int64_t cap, int64_t *n);
 

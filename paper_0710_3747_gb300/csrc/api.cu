@@ -2680,6 +2680,50 @@ static int persist_check(spinrp_batch *b) {
   return SPINRP_OK;
 }
 
+extern "C" int spinrp_batch_persist_timeout_check(spinrp_batch *b, int64_t steps, double *seconds) {
+  if (!b || steps < 1) return fail(SPINRP_EINVAL, "batch_persist_timeout_check: bad argument");
+  if (!b->persist_K || !b->ready) return fail(SPINRP_ESTATE, "batch_persist_timeout_check: no persistent groups");
+  PersistPlan pp;
+  if (!build_persist_plan(b, steps, &pp) || pp.nregions < 1 || pp.start[1] < 2)
+    return fail(SPINRP_EUNSUPPORTED, "batch_persist_timeout_check: plan too small");
+  // the plan on the device; the queue starts at the first item of sweep 1,
+  // so the sweep-0 tiles every item waits for never run
+  CUDA_TRY(cudaMemcpyAsync(b->d_persist, &pp, sizeof pp, cudaMemcpyHostToDevice, b->stream));
+  b->plan_steps = -1;  // the next evolve uploads its own plan and graph
+  if (b->pgraph) cudaGraphExecDestroy(b->pgraph), b->pgraph = nullptr;
+  int njobs = 0;
+  for (const BatchGroup &g : b->groups)
+    if (in_persist(b, g)) njobs += (int)g.jobs.size();
+  CUDA_TRY(cudaMemsetAsync(persist_queue(b), 0, 256 + sizeof(unsigned) * (size_t)njobs, b->stream));
+  const unsigned long long first = pp.per[0];
+  CUDA_TRY(cudaMemcpyAsync(persist_queue(b), &first, sizeof first, cudaMemcpyHostToDevice, b->stream));
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  cudaEventRecord(e0, b->stream);
+  const unsigned nt = 1u << (b->persist_K - 6);
+  persist_kernel<6><<<b->persist_blocks, nt, size_t(8) << b->persist_K, b->stream>>>(
+      (const PersistPlan *)b->d_persist, persist_queue(b), persist_done(b), persist_err(b), b->persist_blocks);
+  cudaEventRecord(e1, b->stream);
+  ++g_launches;
+  const cudaError_t le = cudaGetLastError();
+  int err = 0;
+  cudaError_t ce = cudaMemcpyAsync(&err, persist_err(b), sizeof err, cudaMemcpyDeviceToHost, b->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);
+  float ms = 0.f;
+  if (ce == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (le != cudaSuccess || ce != cudaSuccess)
+    return fail(SPINRP_ECUDA, "batch_persist_timeout_check: %s", cudaGetErrorString(le != cudaSuccess ? le : ce));
+  if (seconds) *seconds = ms / 1e3;
+  // clear the error word again: the batch's series are unchanged (no tile ran)
+  CUDA_TRY(cudaMemsetAsync(persist_err(b), 0, sizeof(int), b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  return err ? fail(SPINRP_ETIMEOUT, "batch_persist_timeout_check: the waits ran out as intended")
+             : fail(SPINRP_ECUDA, "batch_persist_timeout_check: no wait ran out");
+}
+
 extern "C" int spinrp_batch_set_persistent(spinrp_batch *b, int on) {
   if (!b || (on != 0 && on != 1)) return fail(SPINRP_EINVAL, "batch_set_persistent: bad argument");
   b->persist = on != 0;

@@ -17,7 +17,7 @@ namespace spinrp {
 
 constexpr int kMaxPersistGroups = 16;
 constexpr int kMaxSteadyPasses = 64;
-constexpr unsigned kPersistWaitLimit = 1u << 23;  // polls of about 0.1-0.3 us: about a second
+constexpr unsigned kPersistWaitLimit = 1u << 21;  // polls, each an L2 round trip and a short sleep: about a second
 
 struct PersistGroup {
   int M, K;

@@ -500,6 +500,8 @@ _BATCH_SIG = {
     "spinrp_batch_init_product_phase": ([ctypes.c_void_p], ctypes.c_int),
     "spinrp_batch_evolve": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
     "spinrp_batch_set_persistent": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "spinrp_batch_persist_timeout_check": ([ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)],
+                                           ctypes.c_int),
     "spinrp_batch_polarization": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                    ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "spinrp_batch_ensemble": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -548,6 +550,13 @@ class Batch:
         or one launch per sweep (False, the default)."""
         _check(_batch_lib().spinrp_batch_set_persistent(self._h, int(bool(on))))
         return self
+
+    def persist_timeout_check(self, steps: int = 4) -> tuple[int, float]:
+        """Diagnostic: a persistent launch whose waits all run out (see
+        include/spinrp.h); returns (status code, launch seconds)."""
+        sec = ctypes.c_double()
+        rc = _batch_lib().spinrp_batch_persist_timeout_check(self._h, int(steps), ctypes.byref(sec))
+        return rc, sec.value
 
     def init_random_phase(self):
         _check(_batch_lib().spinrp_batch_init_random_phase(self._h))

@@ -139,3 +139,37 @@ def test_persistent_launch_equals_per_sweep_launches(K):
         j = jobs[k]
         Pw, _, _ = oracle.run(j.J, j.htype, j.seed, 0.02, 26, threads=os.cpu_count() or 1)
         assert np.max(np.abs(Pp[k] - Pw)) <= 1e-4, k
+
+
+def test_persistent_waits_are_bounded():
+    """Failure detection without a GPU fault: a persistent launch whose queue
+    starts past the first sweep has every wait run out; the blocks give up
+    within the poll limit (about a second), the status reads
+    SPINRP_ETIMEOUT, no tile was touched, and the batch then evolves exactly
+    as a batch that never saw the failed launch."""
+    spinrp.lib()
+    jobs = [W.Job(W.star_dipolar(15 + (k % 2), 300 + k), W.DIPOLAR, seed=50 + k, dt=0.02, steps=0)
+            for k in range(6)]
+
+    def make():
+        systems = []
+        for j in jobs:
+            s = spinrp.System(j.J, j.htype)
+            s.set_tile("c64", 13)
+            s.set_regbits(6)
+            systems.append(s)
+        b = spinrp.Batch(systems, [j.seed for j in jobs], "c64", series_cap=16)
+        return b.set_persistent(True)
+
+    b = make()
+    b.init_random_phase()
+    rc, sec = b.persist_timeout_check(4)
+    assert rc == spinrp.ETIMEOUT
+    assert 0.0 < sec < 30.0
+    b.evolve(0.02, 6)
+    ref = make()
+    ref.init_random_phase().evolve(0.02, 6)
+    for k in range(len(jobs)):
+        assert np.array_equal(b.polarization(k), ref.polarization(k)), k
+    b.close()
+    ref.close()
