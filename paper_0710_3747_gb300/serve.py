@@ -113,7 +113,8 @@ def _chunk_done(a: _Active) -> bool:
 def run_stream(jobs: list[W.Job], prec: str = "c64", max_active: int = 16,
                hbm_budget: int | None = None, chunk: int = 20, tile_K: int | None = None,
                realtime: bool = True, start_fn=None, finish_fn=None, footprint_fn=None,
-               trace: list | None = None, depth: int = 2, priorities: bool = True) -> list[Result]:
+               trace: list | None = None, depth: int = 2, priorities: bool = True,
+               policy: str = "fifo") -> list[Result]:
     """Serve `jobs` (sorted by arrival) with continuous batching.
 
     realtime: arrivals follow the wall clock (t = 0 at the call); otherwise all
@@ -123,7 +124,9 @@ def run_stream(jobs: list[W.Job], prec: str = "c64", max_active: int = 16,
     `depth` chunks of `chunk` Trotter steps in flight per job, polls their
     completion events without blocking, and retires a job (P(t) to the host,
     memory and slot freed) as soon as its last chunk has finished.  Each job's
-    footprint is computed once.  start_fn / finish_fn / footprint_fn replace
+    footprint is computed once.  policy "fifo" admits arrived jobs in arrival
+    order; "sjf" admits, among the arrived jobs, the one with the least work
+    (amplitude-gate updates) first.  start_fn / finish_fn / footprint_fn replace
     the device calls (host-side tests); `trace`, when given, receives
     ("admit" | "chunk" | "done", job index, bytes in use)."""
     footprint_fn = footprint_fn or footprint
@@ -144,6 +147,20 @@ def run_stream(jobs: list[W.Job], prec: str = "c64", max_active: int = 16,
     while k < len(pending) or active:
         progress = False
         # admit arrived jobs while slots and memory allow
+        if policy == "sjf" and k < len(pending):
+            # order the arrived, not yet admitted jobs by work (least first)
+            t_now = now()
+            m = k
+            while m < len(pending) and (not realtime or pending[m].arrival <= t_now):
+                m += 1
+            if m - k > 1:
+                order = sorted(range(k, m), key=lambda q: (job_work(pending[q]), q))
+                moved = [pending[q] for q in order]
+                keys = [need.pop(q, None) for q in order]
+                pending[k:m] = moved
+                for off, v in enumerate(keys):
+                    if v is not None:
+                        need[k + off] = v
         while k < len(pending) and len(active) < max_active:
             j = pending[k]
             if realtime and j.arrival > now():
@@ -245,6 +262,8 @@ def main(argv=None):
     ap.add_argument("--saturated", action="store_true",
                     help="every job arrives at t = 0 (a full queue): throughput is not bound by arrivals")
     ap.add_argument("--no-priorities", action="store_true", help="all job streams at the default priority")
+    ap.add_argument("--policy", choices=["fifo", "sjf"], default="fifo",
+                    help="admission order among arrived jobs: arrival, or least work first")
     args = ap.parse_args(argv)
     tile_K = args.tile_K or None
     import torch
@@ -262,7 +281,7 @@ def main(argv=None):
             j.arrival = 0.0
     t = time.perf_counter()
     mix = run_stream(jobs, args.prec, max_active=args.max_active, chunk=args.chunk, tile_K=tile_K,
-                     realtime=realtime, priorities=not args.no_priorities)
+                     realtime=realtime, priorities=not args.no_priorities, policy=args.policy)
     torch.cuda.synchronize()
     wall_mix = time.perf_counter() - t
     t = time.perf_counter()

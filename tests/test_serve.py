@@ -152,3 +152,18 @@ def test_full_stream_sampled_jobs_match_oracle():
         worst = max(worst, err)
         assert err <= 1e-4, (j.kind, j.M, j.steps, err)
     print(f"20 sampled jobs (M {min(j.M for j in pick)}..{max(j.M for j in pick)}): max |dP| = {worst:.2e}")
+
+
+def test_sjf_admits_least_work_first():
+    """With every job arrived, policy "sjf" admits in order of work (2^M x
+    bonds x steps), least first; each job still gets exactly its steps."""
+    jobs = _jobs(10, seed=8)
+    trace = []
+    out = serve.run_stream(jobs, max_active=1, hbm_budget=10**9, chunk=5, realtime=False,
+                           start_fn=_fake_start, finish_fn=_fake_finish,
+                           footprint_fn=lambda j, p: j.meta["bytes"], trace=trace, policy="sjf")
+    for r, j in zip(out, jobs):
+        assert r.P[0] == j.steps
+    admitted = [idx for ev, idx, _ in trace if ev == "admit"]
+    work = {j.meta["index"]: serve.job_work(j) for j in jobs}
+    assert [work[i] for i in admitted] == sorted(work[i] for i in admitted)
