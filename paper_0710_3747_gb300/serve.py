@@ -264,36 +264,46 @@ def main(argv=None):
     ap.add_argument("--no-priorities", action="store_true", help="all job streams at the default priority")
     ap.add_argument("--policy", choices=["fifo", "sjf"], default="fifo",
                     help="admission order among arrived jobs: arrival, or least work first")
+    ap.add_argument("--mode", choices=["both", "continuous", "sequential"], default="both",
+                    help="which modes to run (one per process keeps each run's device state apart)")
     args = ap.parse_args(argv)
     tile_K = args.tile_K or None
     import torch
     spinrp.lib()
     rate = args.rate
-    if rate <= 0:
+    if rate <= 0 and not args.saturated:
         probe = W.serve_stream(n=20, seed=args.seed + 1, rate=1e9, m_cap=args.m_cap)
         t = time.perf_counter()
         run_sequential(probe, args.prec, tile_K=tile_K, realtime=False)
         rate = 0.7 * len(probe) / (time.perf_counter() - t)
-    jobs = W.serve_stream(n=args.jobs, seed=args.seed, rate=rate, m_cap=args.m_cap)
+    jobs = W.serve_stream(n=args.jobs, seed=args.seed, rate=rate if rate > 0 else 1.0, m_cap=args.m_cap)
     realtime = not args.saturated
     if args.saturated:
         for j in jobs:
             j.arrival = 0.0
-    t = time.perf_counter()
-    mix = run_stream(jobs, args.prec, max_active=args.max_active, chunk=args.chunk, tile_K=tile_K,
-                     realtime=realtime, priorities=not args.no_priorities, policy=args.policy)
-    torch.cuda.synchronize()
-    wall_mix = time.perf_counter() - t
-    t = time.perf_counter()
-    seq = run_sequential(jobs, args.prec, tile_K=tile_K, realtime=realtime)
-    wall_seq = time.perf_counter() - t
-    same = max(float(np.max(np.abs(a.P - b.P))) for a, b in zip(mix, seq))
     work = sum(job_work(j) for j in jobs)
     Ms = [j.M for j in jobs]
-    print(json.dumps({"jobs": len(jobs), "saturated": args.saturated, "rate_per_s": None if args.saturated else rate,
-                      "M_range": [min(Ms), max(Ms)], "amp_gate_updates": work,
-                      "continuous": summary(mix, wall_mix), "sequential": summary(seq, wall_seq),
-                      "max_dP_mix_vs_alone": same}))
+    out = {"jobs": len(jobs), "saturated": args.saturated, "rate_per_s": None if args.saturated else rate,
+           "M_range": [min(Ms), max(Ms)], "amp_gate_updates": work, "policy": args.policy}
+    res = {}
+    for mode in ("continuous", "sequential"):
+        if args.mode not in ("both", mode):
+            continue
+        t = time.perf_counter()
+        if mode == "continuous":
+            r = run_stream(jobs, args.prec, max_active=args.max_active, chunk=args.chunk, tile_K=tile_K,
+                           realtime=realtime, priorities=not args.no_priorities, policy=args.policy)
+        else:
+            r = run_sequential(jobs, args.prec, tile_K=tile_K, realtime=realtime)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t
+        res[mode] = r
+        out[mode] = summary(r, wall)
+        out[mode]["amp_gate_updates_per_s"] = work / wall
+    if len(res) == 2:
+        out["max_dP_mix_vs_alone"] = max(float(np.max(np.abs(a.P - b.P)))
+                                         for a, b in zip(res["continuous"], res["sequential"]))
+    print(json.dumps(out))
     return 0
 
 
