@@ -173,3 +173,27 @@ def test_persistent_waits_are_bounded():
         assert np.array_equal(b.polarization(k), ref.polarization(k)), k
     b.close()
     ref.close()
+
+
+def test_batch_autotuner_sets_a_measured_width():
+    """spinrp.autotune_batch times the whole batch at each candidate tile width
+    of its multi-tile systems, keeps the fastest and sets it (six register
+    bits) on those systems; the tuned batch still evolves as the oracle does."""
+    spinrp.lib()
+    jobs = [W.Job(W.star_dipolar(15 + (k % 2), 500 + k), W.DIPOLAR, seed=70 + k, dt=0.02, steps=0)
+            for k in range(8)]
+    jobs.append(W.Job(W.star_dipolar(12, 599), W.DIPOLAR, seed=99, dt=0.02, steps=0))
+    systems = [spinrp.System(j.J, j.htype) for j in jobs]
+    r = spinrp.autotune_batch(systems, [j.seed for j in jobs], candidates=(13, 14), probe_steps=4)
+    assert set(r["ms_per_step"]) == {13, 14}
+    assert r["K"] == min(r["ms_per_step"], key=r["ms_per_step"].get)
+    for s in systems[:-1]:
+        assert s.plan_info("c64")["K"] == r["K"]
+    assert systems[-1].plan_info("c64")["K"] == 12  # below the multi-tile sizes: untouched
+    b = spinrp.Batch(systems, [j.seed for j in jobs], "c64", series_cap=11)
+    b.init_random_phase().evolve(0.02, 10)
+    for k in (0, len(jobs) - 1):
+        j = jobs[k]
+        Pw, _, _ = oracle.run(j.J, j.htype, j.seed, 0.02, 10, threads=os.cpu_count() or 1)
+        assert np.max(np.abs(b.polarization(k) - Pw)) <= 1e-4, k
+    b.close()
