@@ -883,9 +883,11 @@ __device__ __forceinline__ uint32_t thread_origin(const PhaseDesc &ph, int tid, 
 // The diagonal phase e^{-i tau D}, amplitude by amplitude in shared memory.
 // ORIENT: amplitudes of odd orientation are stored (Im, Re) and take the
 // conjugate phase (the stored word is i conj(psi), and i conj(psi e^{ia}) =
-// i conj(psi) e^{-ia}).
+// i conj(psi) e^{-ia}).  Kept out of line: only systems with S^zS^z terms run
+// it, and the sweep's gate code stays smaller (measured 2 % faster on
+// dipolar stars, unchanged on XY ladders).
 template <int RB, bool ORIENT, typename Sync>
-__device__ __forceinline__ void diag_phase(float2 *tile2, const PassDesc &d, const PhaseDesc &ph,
+__device__ __noinline__ void diag_phase(float2 *tile2, const PassDesc &d, const PhaseDesc &ph,
                                            const ROpRes &op, uint64_t base, int tid, int lognt, int M,
                                            const uint64_t *__restrict__ qdiag, uint64_t *sH, uint64_t *sQ,
                                            uint64_t *sOut, uint32_t s0, const uint32_t (&sm)[RB], Sync sync) {
