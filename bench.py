@@ -372,6 +372,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     nb = len(sysm.bonds())
     info = sysm.plan_info(prec)
     st = spinrp.State(sysm, prec, series_cap=job.steps + 1)
+    if args.no_pipeline:
+        st.set_pipeline(False)
+    pipelined = prec == "c64" and st.pipeline()
     if args.sites:
         st.set_sites(True)  # P_{q1}(t) of every spin after every step
     stream = torch.cuda.current_stream()
@@ -451,21 +454,28 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     sweep_avg_s = sweep_ms / max(sweep_n, 1) / 1e3
     achieved = alg_bytes_per_launch / sweep_avg_s / 1e9
     kernel_bw = sweep_bytes / sweep_avg_s / 1e9
+    if prec == "c64":
+        kname = "pipe_kernel<6, 13>" if pipelined else ("sweep2_kernel" if info["K"] >= 10 else "sweep_kernel<float>")
+    else:
+        kname = "sweep2d_kernel" if info["K"] >= 10 else "sweep_kernel<double>"
+    # DRAM bytes per launch from an ncu capture, used while the kernel and its
+    # sources are the ones the capture measured
     traffic = None
     tfile = ROOT / "profiles" / f"traffic_{args.workload}_{prec}.json"
     if tfile.exists():
         try:
             tinfo = json.loads(tfile.read_text())
             import hashlib
-            h = hashlib.sha256((ROOT / "paper_0710_3747_gb300" / "csrc" / "kernels.cuh").read_bytes()).hexdigest()
-            if tinfo.get("kernels_sha256") == h:
+            hs = hashlib.sha256()
+            for f in tinfo.get("sources", ["kernels.cuh"]):
+                hs.update((ROOT / "paper_0710_3747_gb300" / "csrc" / f).read_bytes())
+            if tinfo.get("sources_sha256") == hs.hexdigest() and tinfo.get("kernel") == kname:
                 traffic = tinfo.get("dram_bytes_per_launch")
         except Exception:
             traffic = None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": ("sweep2_kernel" if info["K"] >= 10 else "sweep_kernel<float>") if prec == "c64"
-                else ("sweep2d_kernel" if info["K"] >= 10 else "sweep_kernel<double>"),
+                "kernel": kname,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
                 "algorithmic_bytes_per_launch": alg_bytes_per_launch,
                 "algorithmic_bytes": (f"minimal-sweep bytes of a Trotter step ({min_sweeps} sweeps x 2 x "
@@ -506,6 +516,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "config": {"workload": wname, "M": job.M, "bonds": nb, "trotter_steps": job.steps,
                    "dt": job.dt, "amplitudes": "complex64" if prec == "c64" else "complex128",
                    "tile_K": info["K"], "sweeps_per_step": info["sweeps_per_step"],
+                   "pipelined_sweeps": pipelined,
                    "autotuned": None if tuned is None else {"K": tuned["K"], "rb": tuned["rb"]},
                    "all_site_readout": bool(args.sites),
                    "initial_state": "product" if args.product else "entangled",
@@ -617,6 +628,8 @@ def main():
     ap.add_argument("--tile-K", type=int, default=0, help="tile width override (autotuner knob)")
     ap.add_argument("--regbits", type=int, default=0, help="register bits per phase, 5 or 6 (autotuner knob)")
     ap.add_argument("--sites", action="store_true", help="all-site readout P_{q1}(t) of every spin each step")
+    ap.add_argument("--no-pipeline", action="store_true",
+                    help="one tile per block instead of the pipelined sweep (for comparison)")
     ap.add_argument("--product", action="store_true", help="the paper's product random state instead of the entangled one")
     ap.add_argument("--autotune", action="store_true",
                     help="time tile / register-bit candidates first and run the fastest (spinrp.autotune)")

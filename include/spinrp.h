@@ -307,6 +307,35 @@ int spinrp_state_layout(const spinrp_state *st, int32_t *layout, void **psi);
  * state stored plainly.  Host only. */
 int spinrp_state_orientation(const spinrp_state *st, uint64_t *black);
 
+/* Pipelined sweeps (no counterpart in the paper; the same Trotter steps of
+ * Sec. 3, Eq. 3, scheduled differently).  A complex64 state whose plan uses
+ * 13-spin tiles and six register bits, plainly stored, with at least four
+ * tiles per SM (M >= 23 on GB300), runs each sweep as one persistent launch
+ * of one block per SM: a producer warp gathers tiles into three shared-memory
+ * buffers and writes them back while two compute groups apply the sweep's
+ * gates, so the state's streaming through HBM overlaps the arithmetic.
+ * on = 1 (the default) uses it where the plan takes it, on = 0 the
+ * one-tile-per-block sweep; the amplitudes and series are the same bit for
+ * bit.  Takes effect at the next evolve.  Host only.  Errors: SPINRP_EINVAL.
+ * The pipeline's hand-over waits are bounded (2 s each); one that gives up
+ * records NaN for that step's P and norm and sets the state's error word,
+ * which spinrp_polarization (site 1) and spinrp_norm_series then report as
+ * SPINRP_ETIMEOUT. */
+int spinrp_state_set_pipeline(spinrp_state *st, int on);
+
+/* *on = 1 when the state's sweeps run pipelined (the setting is on and the
+ * plan takes it), else 0.  Host only.  Errors: SPINRP_EINVAL. */
+int spinrp_state_pipeline(const spinrp_state *st, int *on);
+
+/* Diagnostic of the pipelined sweep's bounded waits (no counterpart in the
+ * paper): one launch in which the producer issues no copies, so every wait
+ * gives up after its time limit and every block returns; reports
+ * SPINRP_ETIMEOUT (with the launch's duration in *seconds, if not NULL) --
+ * SPINRP_ECUDA if no wait ran out -- and clears the error word again.  The
+ * amplitudes and the series are untouched.  SPINRP_ESTATE when the state's
+ * plan does not take the pipelined sweep.  Synchronizes. */
+int spinrp_state_pipeline_timeout_check(spinrp_state *st, double *seconds);
+
 /* ---- batches of independent jobs ------------------------------------------ */
 
 /* A batch evolves many independent random-phase states at once: disorder

@@ -19,6 +19,7 @@
 #include "internal.h"
 #include "kernels.cuh"
 #include "persist.cuh"
+#include "pipe.cuh"
 #include "sectors.cuh"
 #include "sweep2d.cuh"
 
@@ -425,6 +426,8 @@ struct spinrp_state {
   JobPtrs *d_job = nullptr;   // this state's pointer table (one job)
   JobPtrs hjob{};             // the same, host copy (passed with each sweep launch)
   unsigned prefetch_ahead = 0;  // L2 prefetch distance of the register-blocked sweep
+  unsigned pipe_blocks = 0;   // blocks of the pipelined sweep, 0 when the plan does not take it
+  bool pipe_req = true;       // pipelined sweeps where the plan takes them
   uint64_t orient_black = 0;  // oriented state: first-colour spins (logical), else 0
   uint64_t orient_phys = 0;   // the same as physical positions of the step-boundary layout
   int64_t *d_step = nullptr;  // device series counter
@@ -950,6 +953,7 @@ static void free_state(spinrp_state *st) {
 // Largest dynamic shared memory of resident_kernel: 227 KiB per block less
 // its static arrays (diagonal-phase and reduction scratch, under 4 KiB).
 constexpr size_t kResidentMaxSmem = size_t(223) * 1024;
+constexpr size_t kPipeSmem = size_t(3) << 16;  // pipe_kernel<6, 13>: three 64 KiB tile buffers
 
 template <typename R>
 static int set_smem_limits() {
@@ -969,6 +973,7 @@ static int set_smem_limits() {
     CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6, false, true>, a, 8 << 14));
     CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<5, true, true>, a, 8 << 14));
     CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6, true, true>, a, 8 << 14));
+    CUDA_TRY(cudaFuncSetAttribute(pipe_kernel<6, 13>, a, (int)kPipeSmem));
     CUDA_TRY(cudaFuncSetAttribute(resident_kernel<5, false>, a, (int)kResidentMaxSmem));
     CUDA_TRY(cudaFuncSetAttribute(resident_kernel<5, true>, a, (int)kResidentMaxSmem));
     CUDA_TRY(cudaFuncSetAttribute(resident_kernel<6, false>, a, (int)kResidentMaxSmem));
@@ -1005,6 +1010,30 @@ static unsigned sweep2_resident(int prec, int rb, int K, bool oriented) {
     return 0;
   }
   return (unsigned)(per * sms);
+}
+
+// Blocks of the pipelined sweep (pipe_kernel, one per SM) for a state's plan,
+// or 0 when the plan does not take it: complex64, register-blocked with six
+// register bits and 13-spin tiles, plain storage, and at least four tiles per
+// SM so that the three-buffer pipeline fills.
+static unsigned pipe_grid(int prec, const Plan &plan, const PassSet &ps, int M) {
+  if (prec != SPINRP_C64 || !ps.phased || ps.rb != 6 || plan.K != 13 || ps.oriented) return 0;
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pipe_kernel<6, 13>, kPipeThreads, kPipeSmem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (per < 1 || (1ull << (M - 13)) < 4ull * (unsigned long long)sms) return 0;
+  return (unsigned)sms;
+}
+
+// The state's error word of the pipelined sweep: 128 bytes into the 256-byte
+// ticket area (ticket at +0, series counter at +64), cleared with it.
+static int *pipe_err_word(spinrp_state *st) {
+  return reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(st->ticket) + 128);
 }
 
 extern "C" int spinrp_state_create(const spinrp_system *sys, int prec, void *stream,
@@ -1119,6 +1148,7 @@ extern "C" int spinrp_state_create(const spinrp_system *sys, int prec, void *str
     return rc;
   }
   if (st->ps.phased) st->prefetch_ahead = sweep2_resident(prec, st->ps.rb, st->plan.K, st->ps.oriented);
+  st->pipe_blocks = pipe_grid(prec, st->plan, st->ps, st->M);
   if (st->ps.oriented) {
     st->orient_black = st->ps.black;
     for (int q = 0; q < st->M; ++q)
@@ -1275,6 +1305,55 @@ extern "C" int spinrp_state_orientation(const spinrp_state *st, uint64_t *black)
   return SPINRP_OK;
 }
 
+extern "C" int spinrp_state_set_pipeline(spinrp_state *st, int on) {
+  if (!st || (on != 0 && on != 1)) return fail(SPINRP_EINVAL, "state_set_pipeline: bad argument");
+  if (st->pipe_req != (on != 0)) {
+    // cached graphs hold the launches of the other sweep kernel
+    for (cudaGraphExec_t &g : st->graphs)
+      if (g) cudaGraphExecDestroy(g), g = nullptr;
+    st->pipe_req = on != 0;
+  }
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_state_pipeline(const spinrp_state *st, int *on) {
+  if (!st || !on) return fail(SPINRP_EINVAL, "state_pipeline: bad argument");
+  *on = (st->pipe_req && st->pipe_blocks > 0) ? 1 : 0;
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_state_pipeline_timeout_check(spinrp_state *st, double *seconds) {
+  if (!st) return fail(SPINRP_EINVAL, "state_pipeline_timeout_check: state is NULL");
+  if (!st->pipe_blocks || st->ps.desc.empty())
+    return fail(SPINRP_ESTATE, "state_pipeline_timeout_check: the state's sweeps do not run pipelined");
+  int *err = pipe_err_word(st);
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  cudaEventRecord(e0, st->stream);
+  // probe = 1: the producer issues no copies, so every wait of every block
+  // runs out; nothing is written to the amplitudes or the series
+  pipe_kernel<6, 13><<<st->pipe_blocks, kPipeThreads, kPipeSmem, st->stream>>>(
+      st->d_job, static_cast<float2 *>(st->psi), st->hjob.sops, st->ps.desc[0], st->phases, st->M, err, 1);
+  cudaEventRecord(e1, st->stream);
+  ++g_launches;
+  const cudaError_t le = cudaGetLastError();
+  int flag = 0;
+  cudaError_t ce = cudaMemcpyAsync(&flag, err, sizeof flag, cudaMemcpyDeviceToHost, st->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st->stream);
+  float ms = 0.f;
+  if (ce == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (le != cudaSuccess || ce != cudaSuccess)
+    return fail(SPINRP_ECUDA, "state_pipeline_timeout_check: %s", cudaGetErrorString(le != cudaSuccess ? le : ce));
+  if (seconds) *seconds = ms / 1e3;
+  CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st->stream));
+  CUDA_TRY(cudaStreamSynchronize(st->stream));
+  return flag ? fail(SPINRP_ETIMEOUT, "state_pipeline_timeout_check: the waits ran out as intended")
+              : fail(SPINRP_ECUDA, "state_pipeline_timeout_check: no wait ran out");
+}
+
 extern "C" int spinrp_state_layout(const spinrp_state *st, int32_t *layout, void **psi) {
   if (!st) return fail(SPINRP_EINVAL, "layout: state is NULL");
   if (layout)
@@ -1302,6 +1381,8 @@ struct LaunchCtx {
   int sites = 0;                 // all-site readout after every reducing sweep
   unsigned prefetch_ahead = 0;   // sweep blocks resident at once (L2 prefetch distance), 0 = off
   bool resident = false;         // whole state kept in shared memory for every step (resident_kernel)
+  unsigned pipe_blocks = 0;      // > 0: one-job sweeps of the plan run as pipe_kernel on this many blocks
+  int *pipe_err = nullptr;       // its error word
   size_t resident_smem = 0;      // its dynamic shared memory
   spinrp_state *prof = nullptr;  // state whose profiling marks to record, if any
 };
@@ -1371,6 +1452,13 @@ static int launch_pass(const LaunchCtx &c, int pass, cudaStream_t stream, bool l
     const unsigned ahead = c.prefetch_ahead;
     const ROpRes *sops1 = c.njobs == 1 ? c.job0.sops : nullptr;
     const int code = (c.rb == 6 ? 4 : 0) | (sites ? 2 : 0) | (c.oriented ? 1 : 0);
+    if (c.pipe_blocks && code == 4 && K == 13 && c.njobs == 1) {
+      pipe_kernel<6, 13><<<c.pipe_blocks, kPipeThreads, kPipeSmem, stream>>>(
+          c.jobs, psi1, sops1, pd, c.phases, c.M, c.pipe_err, 0);
+      CUDA_TRY(cudaGetLastError());
+      if (live && c.prof) prof_mark(c.prof, SPINRP_KERNEL_SWEEP);
+      return SPINRP_OK;
+    }
 #define SW2(RB_, S_, O_) \
   sweep2_kernel<RB_, S_, O_><<<grid, 1 << (K - RB_), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M, ahead)
     switch (code) {
@@ -1548,6 +1636,8 @@ static LaunchCtx state_ctx(spinrp_state *st) {
   c.resident_smem = resident_bytes(st->plan, st->ps, st->prec, st->sites);
   c.resident = c.resident_smem > 0;
   c.prefetch_ahead = st->prefetch_ahead;
+  c.pipe_blocks = st->pipe_req ? st->pipe_blocks : 0;
+  c.pipe_err = pipe_err_word(st);
   c.segments = st->plan.segments();
   c.sweeps_per_step = st->plan.sweeps_per_step();
   c.ps = &st->ps;
@@ -1614,8 +1704,15 @@ static int copy_series(spinrp_state *st, int which, double *out, int64_t cap, in
   std::vector<double> buf(2 * m);
   CUDA_TRY(cudaMemcpyAsync(buf.data(), st->series, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, st->stream));
   st->d2h += (int64_t)sizeof(double) * 2 * m;
+  // a pipelined sweep whose wait gave up recorded NaN and set the error word
+  int perr = 0;
+  if (st->pipe_blocks) {
+    CUDA_TRY(cudaMemcpyAsync(&perr, pipe_err_word(st), sizeof perr, cudaMemcpyDeviceToHost, st->stream));
+    st->d2h += (int64_t)sizeof perr;
+  }
   CUDA_TRY(cudaStreamSynchronize(st->stream));
   for (int64_t k = 0; k < m; ++k) out[k] = buf[2 * k + which];
+  if (perr) return fail(SPINRP_ETIMEOUT, "series: a wait of the pipelined sweep gave up");
   return SPINRP_OK;
 }
 

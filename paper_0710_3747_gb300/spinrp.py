@@ -70,6 +70,9 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
             "spinrp_system_set_regbits": ([vp, ctypes.c_int], ctypes.c_int),
             "spinrp_system_set_orientation": ([vp, ctypes.c_int], ctypes.c_int),
             "spinrp_state_orientation": ([vp, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+            "spinrp_state_set_pipeline": ([vp, ctypes.c_int], ctypes.c_int),
+            "spinrp_state_pipeline": ([vp, ip], ctypes.c_int),
+            "spinrp_state_pipeline_timeout_check": ([vp, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "spinrp_system_orientation": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
             "spinrp_system_plan_info": ([vp, ctypes.c_int, ip, ip, ip], ctypes.c_int),
             "spinrp_system_plan_gates": ([vp, ctypes.c_int, i32p, i32p, ctypes.c_int, ip], ctypes.c_int),
@@ -387,6 +390,26 @@ class State:
         m = ctypes.c_uint64()
         _check(lib().spinrp_state_orientation(self._h, ctypes.byref(m)))
         return int(m.value)
+
+    def set_pipeline(self, on: bool = True):
+        """Pipelined sweeps (one persistent launch per sweep, producer and
+        compute warpgroups) where the plan takes them (True, the default), or
+        one tile per block (False); the results are the same bit for bit."""
+        _check(lib().spinrp_state_set_pipeline(self._h, int(bool(on))))
+        return self
+
+    def pipeline(self) -> bool:
+        """True when the state's sweeps run pipelined."""
+        on = ctypes.c_int()
+        _check(lib().spinrp_state_pipeline(self._h, ctypes.byref(on)))
+        return bool(on.value)
+
+    def pipeline_timeout_check(self) -> tuple[int, float]:
+        """Diagnostic: a pipelined launch whose waits all run out (see
+        include/spinrp.h); returns (status code, launch seconds)."""
+        sec = ctypes.c_double()
+        rc = lib().spinrp_state_pipeline_timeout_check(self._h, ctypes.byref(sec))
+        return rc, sec.value
 
     def device_ptr(self) -> int:
         """Device address of the amplitude buffer."""
