@@ -25,7 +25,7 @@
 // completes when the producer's copies of the tile in buffer k have landed
 // (cp.async arrive-on), done[k] when a group has finished its phases on it.
 // While the groups compute two tiles, the producer writes back the previous
-// one and gathers the next.
+// one, gathers the next and prefetches the one after into L2.
 //
 // Every amplitude goes through the same floating-point operations in the
 // same order as in sweep2_kernel, each tile's (N_up, N_dn) partial is summed
@@ -189,6 +189,10 @@ pipe_kernel(const JobPtrs *__restrict__ jobs, float2 *psi, const ROpRes *sops, c
       if (i < nloc && !probe) {
         sw2::load_tile<RB>(psi, sw2::tile_origin(blockIdx.x + i * G, d, M), d, pt, LOGNT, a_tiles + 8u * TA * b);
         pipe::cp_async_arrive(a_full + 8u * b);
+        // tile i + 1 into L2 while tile i - 2 computes: its gather at the next
+        // step then reads L2 (measured: one tile ahead beats two, three or none)
+        if (i + 1u < nloc)
+          sw2::prefetch_tile<RB>(psi, sw2::tile_origin(blockIdx.x + (i + 1u) * G, d, M), d, pt, LOGNT);
       }
     }
     if (!ok && pt == 0) atomicExch(err, 1);
