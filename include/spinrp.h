@@ -389,6 +389,22 @@ int spinrp_batch_evolve(spinrp_batch *b, double dt, int64_t steps, int order);
  * SPINRP_ETIMEOUT.  Errors: SPINRP_EINVAL. */
 int spinrp_batch_set_persistent(spinrp_batch *b, int on);
 
+/* Pipelined sweeps for a batch's multi-tile groups (no counterpart in the
+ * paper; the same steps scheduled differently, see spinrp_state_set_pipeline):
+ * a group of complex64 jobs with 13-spin tiles and six register bits, plainly
+ * stored, with at least four (job, tile) units per SM, runs each sweep as one
+ * persistent launch over all its jobs' tiles.  on = 1 (the default) uses it
+ * where a group takes it, on = 0 one tile per block; the series are the same
+ * bit for bit.  Groups in the persistent launch (spinrp_batch_set_persistent)
+ * keep it.  A hand-over wait that gives up marks the step NaN and sets an
+ * error word that spinrp_batch_polarization and spinrp_batch_ensemble report
+ * as SPINRP_ETIMEOUT.  Host only.  Errors: SPINRP_EINVAL. */
+int spinrp_batch_set_pipeline(spinrp_batch *b, int on);
+
+/* *groups receives the number of the batch's plan groups whose sweeps run
+ * pipelined.  Host only.  Errors: SPINRP_EINVAL. */
+int spinrp_batch_pipeline(const spinrp_batch *b, int *groups);
+
 /* Diagnostic of the persistent launch's bounded waits (no counterpart in the
  * paper): runs the launch for a `steps`-step plan with its queue started past
  * the first sweep, so every item waits for tiles that never run; each wait

@@ -953,7 +953,7 @@ static void free_state(spinrp_state *st) {
 // Largest dynamic shared memory of resident_kernel: 227 KiB per block less
 // its static arrays (diagonal-phase and reduction scratch, under 4 KiB).
 constexpr size_t kResidentMaxSmem = size_t(223) * 1024;
-constexpr size_t kPipeSmem = size_t(3) << 16;  // pipe_kernel<6, 13>: three 64 KiB tile buffers
+constexpr size_t kPipeSmem = size_t(3) << 16;  // pipe_kernel<6, 13, *>: three 64 KiB tile buffers
 
 template <typename R>
 static int set_smem_limits() {
@@ -973,7 +973,8 @@ static int set_smem_limits() {
     CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6, false, true>, a, 8 << 14));
     CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<5, true, true>, a, 8 << 14));
     CUDA_TRY(cudaFuncSetAttribute(sweep2_kernel<6, true, true>, a, 8 << 14));
-    CUDA_TRY(cudaFuncSetAttribute(pipe_kernel<6, 13>, a, (int)kPipeSmem));
+    CUDA_TRY(cudaFuncSetAttribute(pipe_kernel<6, 13, false>, a, (int)kPipeSmem));
+    CUDA_TRY(cudaFuncSetAttribute(pipe_kernel<6, 13, true>, a, (int)kPipeSmem));
     CUDA_TRY(cudaFuncSetAttribute(resident_kernel<5, false>, a, (int)kResidentMaxSmem));
     CUDA_TRY(cudaFuncSetAttribute(resident_kernel<5, true>, a, (int)kResidentMaxSmem));
     CUDA_TRY(cudaFuncSetAttribute(resident_kernel<6, false>, a, (int)kResidentMaxSmem));
@@ -1012,21 +1013,23 @@ static unsigned sweep2_resident(int prec, int rb, int K, bool oriented) {
   return (unsigned)(per * sms);
 }
 
-// Blocks of the pipelined sweep (pipe_kernel, one per SM) for a state's plan,
-// or 0 when the plan does not take it: complex64, register-blocked with six
-// register bits and 13-spin tiles, plain storage, and at least four tiles per
-// SM so that the three-buffer pipeline fills.
-static unsigned pipe_grid(int prec, const Plan &plan, const PassSet &ps, int M) {
-  if (prec != SPINRP_C64 || !ps.phased || ps.rb != 6 || plan.K != 13 || ps.oriented) return 0;
+// Blocks of the pipelined sweep (pipe_kernel, one per SM) for the plan of
+// njobs jobs (a state: 1), or 0 when the plan does not take it: complex64,
+// register-blocked with six register bits and 13-spin tiles, more than one
+// tile per job, plain storage, and at least four units (tiles of all jobs)
+// per SM so that the three-buffer pipeline fills.
+static unsigned pipe_grid(int prec, const Plan &plan, const PassSet &ps, int M, int njobs = 1) {
+  if (prec != SPINRP_C64 || !ps.phased || ps.rb != 6 || plan.K != 13 || M <= 13 || ps.oriented) return 0;
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pipe_kernel<6, 13>, kPipeThreads, kPipeSmem) !=
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pipe_kernel<6, 13, false>, kPipeThreads, kPipeSmem) !=
           cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  if (per < 1 || (1ull << (M - 13)) < 4ull * (unsigned long long)sms) return 0;
+  const unsigned long long units = (unsigned long long)njobs << (M - 13);
+  if (per < 1 || units < 4ull * (unsigned long long)sms || units >= (1ull << 32)) return 0;
   return (unsigned)sms;
 }
 
@@ -1333,8 +1336,8 @@ extern "C" int spinrp_state_pipeline_timeout_check(spinrp_state *st, double *sec
   cudaEventRecord(e0, st->stream);
   // probe = 1: the producer issues no copies, so every wait of every block
   // runs out; nothing is written to the amplitudes or the series
-  pipe_kernel<6, 13><<<st->pipe_blocks, kPipeThreads, kPipeSmem, st->stream>>>(
-      st->d_job, static_cast<float2 *>(st->psi), st->hjob.sops, st->ps.desc[0], st->phases, st->M, err, 1);
+  pipe_kernel<6, 13, false><<<st->pipe_blocks, kPipeThreads, kPipeSmem, st->stream>>>(
+      st->d_job, 1, static_cast<float2 *>(st->psi), st->hjob.sops, st->ps.desc[0], st->phases, st->M, err, 1);
   cudaEventRecord(e1, st->stream);
   ++g_launches;
   const cudaError_t le = cudaGetLastError();
@@ -1452,9 +1455,13 @@ static int launch_pass(const LaunchCtx &c, int pass, cudaStream_t stream, bool l
     const unsigned ahead = c.prefetch_ahead;
     const ROpRes *sops1 = c.njobs == 1 ? c.job0.sops : nullptr;
     const int code = (c.rb == 6 ? 4 : 0) | (sites ? 2 : 0) | (c.oriented ? 1 : 0);
-    if (c.pipe_blocks && code == 4 && K == 13 && c.njobs == 1) {
-      pipe_kernel<6, 13><<<c.pipe_blocks, kPipeThreads, kPipeSmem, stream>>>(
-          c.jobs, psi1, sops1, pd, c.phases, c.M, c.pipe_err, 0);
+    if (c.pipe_blocks && code == 4 && K == 13) {
+      if (c.njobs == 1)
+        pipe_kernel<6, 13, false><<<c.pipe_blocks, kPipeThreads, kPipeSmem, stream>>>(
+            c.jobs, 1, psi1, sops1, pd, c.phases, c.M, c.pipe_err, 0);
+      else
+        pipe_kernel<6, 13, true><<<c.pipe_blocks, kPipeThreads, kPipeSmem, stream>>>(
+            c.jobs, c.njobs, nullptr, nullptr, pd, c.phases, c.M, c.pipe_err, 0);
       CUDA_TRY(cudaGetLastError());
       if (live && c.prof) prof_mark(c.prof, SPINRP_KERNEL_SWEEP);
       return SPINRP_OK;
@@ -2350,6 +2357,7 @@ __global__ void ensemble_kernel(const JobPtrs *__restrict__ jobs, int njobs, int
 struct BatchGroup {
   std::vector<int> jobs;  // batch job indices
   int M = 0, nb = 0, max_blocks = 0;
+  unsigned pipe_blocks = 0;  // blocks of the pipelined sweep for this group, 0 when it does not apply
   bool has_diag = false;
   Plan plan;
   PassSet ps;
@@ -2384,6 +2392,9 @@ struct spinrp_batch {
   int64_t plan_steps = -1;             // steps the uploaded plan and its graph are for
   cudaGraphExec_t pgraph = nullptr;
   unsigned persist_blocks = 0;
+  // pipelined sweeps of the eligible multi-tile groups (pipe_kernel)
+  bool pipe_req = true;
+  int *d_pipe_err = nullptr;  // their error word (in dev_common)
 };
 
 static void free_batch(spinrp_batch *b) {
@@ -2622,12 +2633,16 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
   // the LaunchCtx keep pointers to their group's PassSet: fix them now that
   // the group vector no longer moves
   for (BatchGroup &g : b->groups) g.ctx.ps = &g.ps;
-  const size_t common = align256(sizeof(JobPtrs) * njobs) + sizeof(double) * 2 * series_cap;
+  const size_t o_perr = align256(align256(sizeof(JobPtrs) * njobs) + sizeof(double) * 2 * series_cap);
+  const size_t common = o_perr + 256;
   cudaError_t e = cudaMalloc((void **)&b->dev_common, common);
   if (e == cudaSuccess) {
     b->d_all = (JobPtrs *)b->dev_common;
     b->d_ens = (double *)(b->dev_common + align256(sizeof(JobPtrs) * njobs));
-    e = cudaMemcpyAsync(b->d_all, b->hjobs.data(), sizeof(JobPtrs) * njobs, cudaMemcpyHostToDevice, b->stream);
+    b->d_pipe_err = (int *)(b->dev_common + o_perr);
+    e = cudaMemsetAsync(b->d_pipe_err, 0, 256, b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->d_all, b->hjobs.data(), sizeof(JobPtrs) * njobs, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   }
   if (e != cudaSuccess) {
@@ -2641,8 +2656,12 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
     free_batch(b);
     return rc;
   }
-  for (BatchGroup &g : b->groups)
+  for (BatchGroup &g : b->groups) {
     if (g.ps.phased) g.ctx.prefetch_ahead = sweep2_resident(prec, g.ps.rb, g.plan.K, g.ps.oriented);
+    g.pipe_blocks = g.ctx.resident ? 0 : pipe_grid(prec, g.plan, g.ps, g.M, (int)g.jobs.size());
+    g.ctx.pipe_blocks = b->pipe_req ? g.pipe_blocks : 0;
+    g.ctx.pipe_err = b->d_pipe_err;
+  }
   // the persistent launch takes the eligible groups of the most common
   // eligible tile width (jobs counted)
   {
@@ -2769,11 +2788,13 @@ static int persist_evolve(spinrp_batch *b, int64_t steps) {
 // SPINRP_ETIMEOUT when a wait of the last persistent launch gave up
 // (synchronizes the batch's stream).
 static int persist_check(spinrp_batch *b) {
-  if (!b->d_persist || b->plan_steps < 0) return SPINRP_OK;
-  int err = 0;
-  CUDA_TRY(cudaMemcpyAsync(&err, persist_err(b), sizeof err, cudaMemcpyDeviceToHost, b->stream));
+  int err = 0, perr = 0;
+  const bool persisted = b->d_persist && b->plan_steps >= 0;
+  if (persisted) CUDA_TRY(cudaMemcpyAsync(&err, persist_err(b), sizeof err, cudaMemcpyDeviceToHost, b->stream));
+  if (b->d_pipe_err) CUDA_TRY(cudaMemcpyAsync(&perr, b->d_pipe_err, sizeof perr, cudaMemcpyDeviceToHost, b->stream));
   CUDA_TRY(cudaStreamSynchronize(b->stream));
   if (err) return fail(SPINRP_ETIMEOUT, "batch: a persistent-launch wait timed out; the series are invalid");
+  if (perr) return fail(SPINRP_ETIMEOUT, "batch: a wait of a pipelined sweep gave up; the series are invalid");
   return SPINRP_OK;
 }
 
@@ -2819,6 +2840,27 @@ extern "C" int spinrp_batch_persist_timeout_check(spinrp_batch *b, int64_t steps
   CUDA_TRY(cudaStreamSynchronize(b->stream));
   return err ? fail(SPINRP_ETIMEOUT, "batch_persist_timeout_check: the waits ran out as intended")
              : fail(SPINRP_ECUDA, "batch_persist_timeout_check: no wait ran out");
+}
+
+extern "C" int spinrp_batch_set_pipeline(spinrp_batch *b, int on) {
+  if (!b || (on != 0 && on != 1)) return fail(SPINRP_EINVAL, "batch_set_pipeline: bad argument");
+  if (b->pipe_req != (on != 0)) {
+    // cached graphs hold the launches of the other sweep kernel
+    for (cudaGraphExec_t &g : b->graphs)
+      if (g) cudaGraphExecDestroy(g), g = nullptr;
+    b->pipe_req = on != 0;
+    for (BatchGroup &g : b->groups) g.ctx.pipe_blocks = b->pipe_req ? g.pipe_blocks : 0;
+  }
+  return SPINRP_OK;
+}
+
+extern "C" int spinrp_batch_pipeline(const spinrp_batch *b, int *groups) {
+  if (!b || !groups) return fail(SPINRP_EINVAL, "batch_pipeline: bad argument");
+  int n = 0;
+  for (const BatchGroup &g : b->groups)
+    if (b->pipe_req && g.pipe_blocks && !(b->persist && in_persist(b, g))) ++n;
+  *groups = n;
+  return SPINRP_OK;
 }
 
 extern "C" int spinrp_batch_set_persistent(spinrp_batch *b, int on) {

@@ -117,17 +117,55 @@ constexpr int kPipeRegsProducer = 56;
 static_assert(2 * 128 * kPipeRegsCompute + 128 * kPipeRegsProducer <= kPipeThreads * 168,
               "register split above the launch's registers");
 
-// One sweep of one job (complex64, plain storage, spin-1 readout) with
-// 2^(K-RB) = 128 threads per compute group.  jobs[0]: the job's pointers (gate
-// tables, partials, ticket, series); psi and sops are its amplitudes and
-// resolved ops.  err: the job's error word.  probe: the producer issues no
-// copies, so every wait runs out (the check that the waits are bounded;
-// nothing is written to psi or the series).  Dynamic shared memory: three
-// 8 x 2^K byte tile buffers.
-template <int RB, int K>
+// Sum of a job's T tile partials in tile order by the 128 threads t of a
+// group (barrier `sync`), the order reduce_finalize uses for a 128-thread
+// block; thread 0 appends (P, norm) -- NaN after a wait gave up -- at the
+// job's step counter and advances it.  Scratch su/sd: the group's NW doubles.
+template <int NW, typename Sync>
+__device__ __forceinline__ void pipe_finalize(const JobPtrs &jp, unsigned T, int t, const int *err, double *su,
+                                              double *sd, Sync sync) {
+  double u = 0.0, v = 0.0;
+  for (unsigned b = (unsigned)t; b < T; b += 32u * NW) {
+    const double2 p = __ldcg(&jp.partials[b]);
+    u += p.x, v += p.y;
+  }
+  for (int o = 16; o; o >>= 1) {
+    u += __shfl_xor_sync(0xffffffffu, u, o);
+    v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  if ((t & 31) == 0) su[t >> 5] = u, sd[t >> 5] = v;
+  sync();
+  if (t == 0) {
+    double U = 0.0, D = 0.0;
+    for (int w = 0; w < NW; ++w) U += su[w], D += sd[w];
+    const bool bad = *(volatile const int *)err != 0;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    const int64_t slot = *jp.step;
+    jp.series[2 * slot] = bad ? nan : (U - D) / (U + D);
+    jp.series[2 * slot + 1] = bad ? nan : U + D;
+    *jp.step = slot + 1;
+    *jp.ticket = 0u;
+  }
+}
+
+// One sweep (complex64, plain storage, spin-1 readout) with 2^(K-RB) = 128
+// threads per compute group.
+//   BATCH = false: one job; jobs[0] holds its pointers (gate tables,
+//     partials, ticket, series), psi1 and sops1 its amplitudes and resolved
+//     ops; the units are its tiles, and the last block to finish combines
+//     the tile partials.
+//   BATCH = true: njobs jobs of the same plan (jobs[j]); the units are the
+//     (job, tile) pairs, job-major; each job's ops are read from its own
+//     table (global memory), and the block that finishes a job's last tile
+//     (a per-job tile counter) combines that job's partials.
+// err: the error word.  probe: the producer issues no copies, so every wait
+// runs out (the check that the waits are bounded; nothing is written to the
+// amplitudes or the series).  Dynamic shared memory: three 8 x 2^K byte tile
+// buffers.
+template <int RB, int K, bool BATCH>
 __global__ void __launch_bounds__(kPipeThreads, 1)
-pipe_kernel(const JobPtrs *__restrict__ jobs, float2 *psi, const ROpRes *sops, const __grid_constant__ PassDesc d,
-            const PhaseDesc *__restrict__ phases, int M, int *err, int probe) {
+pipe_kernel(const JobPtrs *__restrict__ jobs, int njobs, float2 *psi1, const ROpRes *sops1,
+            const __grid_constant__ PassDesc d, const PhaseDesc *__restrict__ phases, int M, int *err, int probe) {
   constexpr int LOGNT = K - RB;
   constexpr int NT = 1 << LOGNT;   // threads of a group (a warpgroup)
   constexpr int NW = NT / 32;      // warps of a group
@@ -138,27 +176,31 @@ pipe_kernel(const JobPtrs *__restrict__ jobs, float2 *psi, const ROpRes *sops, c
   __shared__ uint64_t sQ[2][kMaxK * kMaxK];
   __shared__ uint64_t sOut[2];
   __shared__ __align__(16) PhaseDesc s_ph[kMaxPassPhases];
-  __shared__ __align__(16) ROpRes s_op[kMaxPassOps];
+  __shared__ __align__(16) ROpRes s_op[BATCH ? 1 : kMaxPassOps];
   __shared__ __align__(8) uint64_t s_full[3], s_done[3];
   __shared__ double s_up[2][NW], s_dn[2][NW];
-  __shared__ int s_last;
+  __shared__ int s_last[2];
 
   const int tid = threadIdx.x;
   const unsigned G = gridDim.x;
-  const unsigned ntiles = 1u << (M - K);
-  const unsigned nloc = blockIdx.x < ntiles ? (ntiles - 1u - blockIdx.x) / G + 1u : 0u;
+  const int lt = M - K;                       // log2 tiles per job
+  const unsigned T = 1u << lt;
+  const unsigned nunits = BATCH ? (unsigned)njobs << lt : T;
+  const unsigned nloc = blockIdx.x < nunits ? (nunits - 1u - blockIdx.x) / G + 1u : 0u;
   const uint32_t a_tiles = (uint32_t)__cvta_generic_to_shared(tiles);
   const uint32_t a_full = (uint32_t)__cvta_generic_to_shared(s_full);
   const uint32_t a_done = (uint32_t)__cvta_generic_to_shared(s_done);
 
-  // the pass's program, once for the whole sweep
+  // the pass's program, once for the whole sweep (one job: its ops too)
   {
     const uint32_t *pw = reinterpret_cast<const uint32_t *>(phases + d.phase0);
     const uint32_t a_ph = (uint32_t)__cvta_generic_to_shared(s_ph);
     const int nw = d.nphases * (int)(sizeof(PhaseDesc) / 4);
     for (int i = tid; i < nw; i += kPipeThreads) sw2::cp_async4(a_ph + 4u * i, pw + i);
-    const uint32_t a_op = (uint32_t)__cvta_generic_to_shared(s_op);
-    for (int i = tid; i < d.nrops; i += kPipeThreads) sw2::cp_async16(a_op + 16u * i, sops + d.rop0 + i);
+    if (!BATCH) {
+      const uint32_t a_op = (uint32_t)__cvta_generic_to_shared(s_op);
+      for (int i = tid; i < d.nrops; i += kPipeThreads) sw2::cp_async16(a_op + 16u * i, sops1 + d.rop0 + i);
+    }
   }
   if (tid == 0)
     for (int k = 0; k < 3; ++k) {
@@ -169,30 +211,37 @@ pipe_kernel(const JobPtrs *__restrict__ jobs, float2 *psi, const ROpRes *sops, c
   __syncthreads();
 
   if (tid >= 2 * NT) {
-    // producer: at step i write back local tile i - 3, then gather tile i
-    // into the buffer it left (i mod 3)
+    // producer: at step i write back local unit i - 3, then gather unit i
+    // into the buffer it left (i mod 3) and prefetch unit i + 1 into L2
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kPipeRegsProducer));
     const int pt = tid - 2 * NT;
+    auto amps = [&](unsigned u) -> float2 * {
+      return BATCH ? static_cast<float2 *>(jobs[u >> lt].psi) : psi1;
+    };
     bool ok = true;
     for (unsigned i = 0; i < nloc + 3u; ++i) {
       const uint32_t b = i % 3u;
       if (i >= 3u) {
-        const unsigned j = i - 3u;
-        const bool late = !pipe::mbar_wait(a_done + 8u * b, (j / 3u) & 1u, err);
+        const unsigned u = blockIdx.x + (i - 3u) * G;
+        const bool late = !pipe::mbar_wait(a_done + 8u * b, ((i - 3u) / 3u) & 1u, err);
         if (pipe::group_any(late, 3u, NT)) {  // one outcome for the group
           ok = false;
           break;
         }
-        sw2::store_tile<RB>(psi, sw2::tile_origin(blockIdx.x + j * G, d, M), d, pt, LOGNT, tiles + b * TA);
+        sw2::store_tile<RB>(amps(u), sw2::tile_origin(u & (T - 1u), d, M), d, pt, LOGNT, tiles + b * TA);
         pipe::SyncNamed{3u, (uint32_t)NT}();  // every read of the buffer before its refill
       }
       if (i < nloc && !probe) {
-        sw2::load_tile<RB>(psi, sw2::tile_origin(blockIdx.x + i * G, d, M), d, pt, LOGNT, a_tiles + 8u * TA * b);
+        const unsigned u = blockIdx.x + i * G;
+        sw2::load_tile<RB>(amps(u), sw2::tile_origin(u & (T - 1u), d, M), d, pt, LOGNT, a_tiles + 8u * TA * b);
         pipe::cp_async_arrive(a_full + 8u * b);
-        // tile i + 1 into L2 while tile i - 2 computes: its gather at the next
-        // step then reads L2 (measured: one tile ahead beats two, three or none)
-        if (i + 1u < nloc)
-          sw2::prefetch_tile<RB>(psi, sw2::tile_origin(blockIdx.x + (i + 1u) * G, d, M), d, pt, LOGNT);
+        // unit i + 1 into L2 while unit i - 2 computes: its gather at the
+        // next step then reads L2 (measured: one unit ahead beats two, three
+        // or none)
+        if (i + 1u < nloc) {
+          const unsigned u1 = u + G;
+          sw2::prefetch_tile<RB>(amps(u1), sw2::tile_origin(u1 & (T - 1u), d, M), d, pt, LOGNT);
+        }
       }
     }
     if (!ok && pt == 0) atomicExch(err, 1);
@@ -200,9 +249,8 @@ pipe_kernel(const JobPtrs *__restrict__ jobs, float2 *psi, const ROpRes *sops, c
     return;
   }
 
-  // compute group g: local tiles g, g + 2, ...
+  // compute group g: local units g, g + 2, ...
   asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kPipeRegsCompute));
-  const JobPtrs jp = jobs[0];
   const int g = tid / NT, gt = tid % NT;
   const uint32_t bar = 1u + (uint32_t)g;
   const pipe::SyncNamed sync{bar, (uint32_t)NT};
@@ -213,65 +261,58 @@ pipe_kernel(const JobPtrs *__restrict__ jobs, float2 *psi, const ROpRes *sops, c
       if (gt == 0) atomicExch(err, 1);
       break;
     }
-    const unsigned tile = blockIdx.x + i * G;
+    const unsigned u = blockIdx.x + i * G;
+    const unsigned tile = u & (T - 1u);
+    const JobPtrs jp = jobs[BATCH ? (u >> lt) : 0u];
+    const ROpRes *ops = BATCH ? jp.sops + d.rop0 : s_op;
     const uint64_t base = sw2::tile_origin(tile, d, M);
     float up = 0.f, dn = 0.f;
-    sw2::run_phases<RB, false, false>(tiles + b * TA, d, s_ph, s_op, base, gt, LOGNT, M, jp.qdiag, up, dn, sH[g],
+    sw2::run_phases<RB, false, false>(tiles + b * TA, d, s_ph, ops, base, gt, LOGNT, M, jp.qdiag, up, dn, sH[g],
                                       sQ[g], &sOut[g], nullptr, sync);
     // run_phases ends with the group's barrier: the tile is finished
     if (gt == 0) pipe::mbar_arrive(a_done + 8u * b);
     if (d.has_reduce) {
       // the tile's partial, summed as reduce_finalize sums a block's
-      double u = (double)up, v = (double)dn;
+      double pu = (double)up, pv = (double)dn;
       for (int o = 16; o; o >>= 1) {
-        u += __shfl_xor_sync(0xffffffffu, u, o);
-        v += __shfl_xor_sync(0xffffffffu, v, o);
+        pu += __shfl_xor_sync(0xffffffffu, pu, o);
+        pv += __shfl_xor_sync(0xffffffffu, pv, o);
       }
-      if ((gt & 31) == 0) s_up[g][gt >> 5] = u, s_dn[g][gt >> 5] = v;
+      if ((gt & 31) == 0) s_up[g][gt >> 5] = pu, s_dn[g][gt >> 5] = pv;
       sync();
       if (gt == 0) {
         double U = 0.0, D = 0.0;
         for (int w = 0; w < NW; ++w) U += s_up[g][w], D += s_dn[g][w];
         jp.partials[tile] = make_double2(U, D);
+        if (BATCH) {
+          // the job's last tile of this sweep combines its partials
+          __threadfence();
+          s_last[g] = (atomicAdd(jp.ticket, 1u) == T - 1u);
+        }
+      }
+      if (BATCH) {
+        sync();
+        if (s_last[g] && !probe) {
+          __threadfence();
+          pipe_finalize<NW>(jp, T, gt, err, s_up[g], s_dn[g], sync);
+        }
       }
     }
   }
-  if (!d.has_reduce || probe) return;
+  if (BATCH || !d.has_reduce || probe) return;
   if (gt == 0) __threadfence();
   const pipe::SyncNamed both{4u, (uint32_t)(2 * NT)};
   both();
 
-  // the last block to finish sums the tile partials in tile order (group 0,
-  // the order reduce_finalize uses for NT threads), appends (P, norm)
+  // one job: the last block to finish combines the tile partials (group 0)
   if (tid == 0) {
-    const unsigned t = atomicAdd(jp.ticket, 1u);
-    s_last = (t == G - 1u);
+    const unsigned t = atomicAdd(jobs[0].ticket, 1u);
+    s_last[0] = (t == G - 1u);
   }
   both();
-  if (!s_last || tid >= NT) return;
+  if (!s_last[0] || tid >= NT) return;
   __threadfence();
-  double u = 0.0, v = 0.0;
-  for (unsigned b = (unsigned)tid; b < ntiles; b += NT) {
-    const double2 p = __ldcg(&jp.partials[b]);
-    u += p.x, v += p.y;
-  }
-  for (int o = 16; o; o >>= 1) {
-    u += __shfl_xor_sync(0xffffffffu, u, o);
-    v += __shfl_xor_sync(0xffffffffu, v, o);
-  }
-  if ((tid & 31) == 0) s_up[0][tid >> 5] = u, s_dn[0][tid >> 5] = v;
-  sync();
-  if (tid == 0) {
-    double U = 0.0, D = 0.0;
-    for (int w = 0; w < NW; ++w) U += s_up[0][w], D += s_dn[0][w];
-    const bool bad = *(volatile int *)err != 0;
-    const double nan = __longlong_as_double(0x7ff8000000000000ll);
-    const int64_t slot = *jp.step;
-    jp.series[2 * slot] = bad ? nan : (U - D) / (U + D);
-    jp.series[2 * slot + 1] = bad ? nan : U + D;
-    *jp.step = slot + 1;
-    *jp.ticket = 0u;
-  }
+  pipe_finalize<NW>(jobs[0], T, tid, err, s_up[0], s_dn[0], sync);
 }
 
 }  // namespace spinrp

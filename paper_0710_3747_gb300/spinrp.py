@@ -523,6 +523,8 @@ _BATCH_SIG = {
     "spinrp_batch_init_product_phase": ([ctypes.c_void_p], ctypes.c_int),
     "spinrp_batch_evolve": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
     "spinrp_batch_set_persistent": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "spinrp_batch_set_pipeline": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "spinrp_batch_pipeline": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "spinrp_batch_persist_timeout_check": ([ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)],
                                            ctypes.c_int),
     "spinrp_batch_polarization": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -573,6 +575,18 @@ class Batch:
         or one launch per sweep (False, the default)."""
         _check(_batch_lib().spinrp_batch_set_persistent(self._h, int(bool(on))))
         return self
+
+    def set_pipeline(self, on: bool = True):
+        """Pipelined sweeps for the multi-tile groups that take them (True,
+        the default) or one tile per block (False); same results bit for bit."""
+        _check(_batch_lib().spinrp_batch_set_pipeline(self._h, int(bool(on))))
+        return self
+
+    def pipeline_groups(self) -> int:
+        """Number of plan groups whose sweeps run pipelined."""
+        n = ctypes.c_int()
+        _check(_batch_lib().spinrp_batch_pipeline(self._h, ctypes.byref(n)))
+        return n.value
 
     def persist_timeout_check(self, steps: int = 4) -> tuple[int, float]:
         """Diagnostic: a persistent launch whose waits all run out (see

@@ -197,3 +197,51 @@ def test_batch_autotuner_sets_a_measured_width():
         Pw, _, _ = oracle.run(j.J, j.htype, j.seed, 0.02, 10, threads=os.cpu_count() or 1)
         assert np.max(np.abs(b.polarization(k) - Pw)) <= 1e-4, k
     b.close()
+
+
+def test_pipelined_batch_sweeps_equal_one_tile_per_block():
+    """Multi-tile groups with enough (job, tile) units run each sweep as one
+    pipelined launch over all their jobs' tiles (units job-major, each job's
+    partials combined by the block that finishes its last tile); every job's
+    P(t) and the ensemble are the same bit for bit as with one tile per block,
+    over two evolve calls (a steady-step graph replayed); a small group stays
+    one tile per block; sampled jobs against the oracle."""
+    spinrp.lib()
+    jobs = []
+    for k in range(24):
+        jobs.append(W.Job(W.star_dipolar(18, 300 + k), W.DIPOLAR, seed=40 + k, dt=0.02, steps=0, kind="s18"))
+    for k in range(6):
+        jobs.append(W.Job(W.star_dipolar(20, 400 + k), W.DIPOLAR, seed=80 + k, dt=0.02, steps=0, kind="s20"))
+    for k in range(8):
+        jobs.append(W.Job(W.ladder(8, 1.0, 0.3 + 0.05 * k), W.XY, seed=120 + k, dt=0.02, steps=0, kind="l16"))
+    for k in range(3):
+        jobs.append(W.Job(W.ladder(11, 1.0, 0.4 + 0.1 * k), W.XY, seed=160 + k, dt=0.02, steps=0, kind="l22"))
+
+    def run(pipe):
+        systems = []
+        for j in jobs:
+            s = spinrp.System(j.J, j.htype)
+            s.set_tile("c64", 13)
+            s.set_regbits(6)
+            systems.append(s)
+        b = spinrp.Batch(systems, [j.seed for j in jobs], "c64", series_cap=32)
+        b.set_pipeline(pipe)
+        groups = b.pipeline_groups()
+        b.init_random_phase().evolve(0.02, 17).evolve(0.02, 9)
+        P = [b.polarization(k) for k in range(len(jobs))]
+        mean, _ = b.ensemble()
+        b.close()
+        return P, mean, groups
+
+    Pp, mp, gp = run(True)
+    Pl, ml, gl = run(False)
+    # stars of 18 spins (24 x 32 tiles), of 20 (6 x 128) and ladders of 22
+    # (3 x 512) are pipelined; 8 ladders of 16 spins (64 tiles) are not
+    assert gp == 3 and gl == 0
+    for k in range(len(jobs)):
+        assert np.array_equal(Pp[k], Pl[k]), k
+    assert np.array_equal(mp, ml)
+    for k in (0, 25, 39):
+        j = jobs[k]
+        Pw, _, _ = oracle.run(j.J, j.htype, j.seed, 0.02, 26, threads=os.cpu_count() or 1)
+        assert np.max(np.abs(Pp[k] - Pw)) <= 1e-4, k
