@@ -298,8 +298,15 @@ extern "C" int spinrp_system_set_regbits(spinrp_system *sys, int rb) {
 // then 12, then 14.  Measured on GB300 against the other widths: ladders of
 // 14, 18, 22, 24 and 30 spins, dipolar stars of 16, 20 and 22 spins, and the
 // batch of 12..22-spin stars (the model's pick was the fastest, or within
-// 2 %, in every case).
+// 2 %, in every case).  Where 13-spin tiles run as the pipelined sweep
+// (pipe_kernel: six register bits, plain storage, at least four units per
+// SM) a sweep costs kPipeSweepCost of the model's sweep: measured per-sweep
+// time of the pipelined 13-spin sweep over the 14-spin one 0.58, 0.59 and
+// 0.72 on dipolar stars of 23, 24 and 26 spins, 0.48, 0.70 and 0.67 on
+// ladders of 24, 26 and 28 spins (K = 13 then the fastest width for all six
+// but the 24-spin ladder, 4 % slower than K = 14 there).
 constexpr int kModelSMs = 152;  // SMs of the GB300 the model was measured on
+constexpr double kPipeSweepCost = 0.6;
 static int make_plan(const spinrp_system &s, int prec, Plan *plan, int njobs = 1) {
   std::string err;
   const int c = low_bits(prec);
@@ -319,7 +326,12 @@ static int make_plan(const spinrp_system &s, int prec, Plan *plan, int njobs = 1
     if (K > s.M) continue;
     Plan p;
     if (!build_plan(s.M, s.bonds, K, c, &p, &err)) continue;
-    const double cost = p.sweeps_per_step() * std::max(std::ldexp(1.0, K), share);
+    double cost = p.sweeps_per_step() * std::max(std::ldexp(1.0, K), share);
+    // the pipelined sweep (pipe_grid's conditions; oriented storage, if asked
+    // for, may leave it out)
+    const bool pipelined = K == 13 && s.M > 13 && (s.regbits == 0 || s.regbits == 6) && s.orient_mode == 0 &&
+                           std::ldexp((double)njobs, s.M - 13) >= 4.0 * kModelSMs;
+    if (pipelined) cost *= kPipeSweepCost;
     if (!have || cost < best) best = cost, *plan = std::move(p), have = true;
   }
   if (!have) return fail(SPINRP_EINVAL, "%s", err.c_str());
@@ -1030,6 +1042,9 @@ static unsigned pipe_grid(int prec, const Plan &plan, const PassSet &ps, int M, 
   }
   const unsigned long long units = (unsigned long long)njobs << (M - 13);
   if (per < 1 || units < 4ull * (unsigned long long)sms || units >= (1ull << 32)) return 0;
+  if (njobs > 1)
+    for (const PassDesc &pd : ps.desc)
+      if (pd.nrops > kPipeBatchOps) return 0;  // a pass's ops must fit a buffer's slice
   return (unsigned)sms;
 }
 
@@ -1337,7 +1352,7 @@ extern "C" int spinrp_state_pipeline_timeout_check(spinrp_state *st, double *sec
   // probe = 1: the producer issues no copies, so every wait of every block
   // runs out; nothing is written to the amplitudes or the series
   pipe_kernel<6, 13, false><<<st->pipe_blocks, kPipeThreads, kPipeSmem, st->stream>>>(
-      st->d_job, 1, static_cast<float2 *>(st->psi), st->hjob.sops, st->ps.desc[0], st->phases, st->M, err, 1);
+      st->d_job, 1, static_cast<float2 *>(st->psi), st->hjob.sops, 0, st->ps.desc[0], st->phases, st->M, err, 1);
   cudaEventRecord(e1, st->stream);
   ++g_launches;
   const cudaError_t le = cudaGetLastError();
@@ -1386,6 +1401,8 @@ struct LaunchCtx {
   bool resident = false;         // whole state kept in shared memory for every step (resident_kernel)
   unsigned pipe_blocks = 0;      // > 0: one-job sweeps of the plan run as pipe_kernel on this many blocks
   int *pipe_err = nullptr;       // its error word
+  JobPtrs batch0{};              // batch group: the first job's pointers ...
+  long long job_stride = 0;      // ... and the byte distance between consecutive jobs' buffers
   size_t resident_smem = 0;      // its dynamic shared memory
   spinrp_state *prof = nullptr;  // state whose profiling marks to record, if any
 };
@@ -1458,10 +1475,18 @@ static int launch_pass(const LaunchCtx &c, int pass, cudaStream_t stream, bool l
     if (c.pipe_blocks && code == 4 && K == 13) {
       if (c.njobs == 1)
         pipe_kernel<6, 13, false><<<c.pipe_blocks, kPipeThreads, kPipeSmem, stream>>>(
-            c.jobs, 1, psi1, sops1, pd, c.phases, c.M, c.pipe_err, 0);
+            c.jobs, 1, psi1, sops1, 0, pd, c.phases, c.M, c.pipe_err, 0);
       else
+      {
         pipe_kernel<6, 13, true><<<c.pipe_blocks, kPipeThreads, kPipeSmem, stream>>>(
-            c.jobs, c.njobs, nullptr, nullptr, pd, c.phases, c.M, c.pipe_err, 0);
+            c.jobs, c.njobs, static_cast<float2 *>(c.batch0.psi), c.batch0.sops, c.job_stride, pd, c.phases, c.M,
+            c.pipe_err, 0);
+        if (pd.has_reduce) {
+          CUDA_TRY(cudaGetLastError());
+          if (live) ++g_launches;
+          pipe_finalize_kernel<<<c.njobs, 128, 0, stream>>>(c.jobs, 1u << (c.M - 13), c.pipe_err);
+        }
+      }
       CUDA_TRY(cudaGetLastError());
       if (live && c.prof) prof_mark(c.prof, SPINRP_KERNEL_SWEEP);
       return SPINRP_OK;
@@ -2625,6 +2650,10 @@ extern "C" int spinrp_batch_create(int njobs, const spinrp_system *const *system
     c.jobs = g.d_jobs;
     if (n == 1) c.job0 = hj[0];
     c.njobs = n;
+    // job k's buffers start per x k bytes after job 0's (the pipelined sweep
+    // computes its addresses from that)
+    c.batch0 = hj[0];
+    c.job_stride = (long long)per;
     c.oriented = g.ps.oriented;
     c.resident_smem = resident_bytes(g.plan, g.ps, prec, false);
     c.resident = c.resident_smem > 0;

@@ -122,11 +122,12 @@ static_assert(2 * 128 * kPipeRegsCompute + 128 * kPipeRegsProducer <= kPipeThrea
 // block; thread 0 appends (P, norm) -- NaN after a wait gave up -- at the
 // job's step counter and advances it.  Scratch su/sd: the group's NW doubles.
 template <int NW, typename Sync>
-__device__ __forceinline__ void pipe_finalize(const JobPtrs &jp, unsigned T, int t, const int *err, double *su,
+__device__ __forceinline__ void pipe_finalize(const double2 *partials, unsigned *ticket, int64_t *step,
+                                              double *series, unsigned T, int t, const int *err, double *su,
                                               double *sd, Sync sync) {
   double u = 0.0, v = 0.0;
   for (unsigned b = (unsigned)t; b < T; b += 32u * NW) {
-    const double2 p = __ldcg(&jp.partials[b]);
+    const double2 p = __ldcg(&partials[b]);
     u += p.x, v += p.y;
   }
   for (int o = 16; o; o >>= 1) {
@@ -140,11 +141,11 @@ __device__ __forceinline__ void pipe_finalize(const JobPtrs &jp, unsigned T, int
     for (int w = 0; w < NW; ++w) U += su[w], D += sd[w];
     const bool bad = *(volatile const int *)err != 0;
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
-    const int64_t slot = *jp.step;
-    jp.series[2 * slot] = bad ? nan : (U - D) / (U + D);
-    jp.series[2 * slot + 1] = bad ? nan : U + D;
-    *jp.step = slot + 1;
-    *jp.ticket = 0u;
+    const int64_t slot = *step;
+    series[2 * slot] = bad ? nan : (U - D) / (U + D);
+    series[2 * slot + 1] = bad ? nan : U + D;
+    *step = slot + 1;
+    *ticket = 0u;
   }
 }
 
@@ -154,17 +155,23 @@ __device__ __forceinline__ void pipe_finalize(const JobPtrs &jp, unsigned T, int
 //     partials, ticket, series), psi1 and sops1 its amplitudes and resolved
 //     ops; the units are its tiles, and the last block to finish combines
 //     the tile partials.
-//   BATCH = true: njobs jobs of the same plan (jobs[j]); the units are the
-//     (job, tile) pairs, job-major; each job's ops are read from its own
-//     table (global memory), and the block that finishes a job's last tile
-//     (a per-job tile counter) combines that job's partials.
+//   BATCH = true: njobs jobs of the same plan (jobs[j]), job j's amplitudes
+//     and resolved ops at psi1 and sops1 plus j x jstride bytes; the units
+//     are the (job, tile) pairs, job-major; the producer copies each unit's job
+//     pointers and resolved ops (at most kPipeBatchOps) into its buffer's
+//     slots of static shared arrays with the tile (the same mbarrier covers
+//     them); each tile leaves its partial, and pipe_finalize_kernel,
+//     launched after a reducing sweep, combines every job's partials.
 // err: the error word.  probe: the producer issues no copies, so every wait
 // runs out (the check that the waits are bounded; nothing is written to the
 // amplitudes or the series).  Dynamic shared memory: three 8 x 2^K byte tile
 // buffers.
+constexpr int kPipeBatchOps = kMaxPassOps / 3;  // resolved ops of a pass, per buffer (batches)
+static_assert(sizeof(JobPtrs) % 8 == 0, "job pointers copied as 8-byte words");
+
 template <int RB, int K, bool BATCH>
 __global__ void __launch_bounds__(kPipeThreads, 1)
-pipe_kernel(const JobPtrs *__restrict__ jobs, int njobs, float2 *psi1, const ROpRes *sops1,
+pipe_kernel(const JobPtrs *__restrict__ jobs, int njobs, float2 *psi1, const ROpRes *sops1, long long jstride,
             const __grid_constant__ PassDesc d, const PhaseDesc *__restrict__ phases, int M, int *err, int probe) {
   constexpr int LOGNT = K - RB;
   constexpr int NT = 1 << LOGNT;   // threads of a group (a warpgroup)
@@ -176,10 +183,12 @@ pipe_kernel(const JobPtrs *__restrict__ jobs, int njobs, float2 *psi1, const ROp
   __shared__ uint64_t sQ[2][kMaxK * kMaxK];
   __shared__ uint64_t sOut[2];
   __shared__ __align__(16) PhaseDesc s_ph[kMaxPassPhases];
-  __shared__ __align__(16) ROpRes s_op[BATCH ? 1 : kMaxPassOps];
+  // one job: the pass's ops; BATCH: three slices of kPipeBatchOps, one per buffer
+  __shared__ __align__(16) ROpRes s_op[kMaxPassOps];
+  __shared__ __align__(16) JobPtrs s_job[BATCH ? 3 : 1];
   __shared__ __align__(8) uint64_t s_full[3], s_done[3];
   __shared__ double s_up[2][NW], s_dn[2][NW];
-  __shared__ int s_last[2];
+  __shared__ int s_last;
 
   const int tid = threadIdx.x;
   const unsigned G = gridDim.x;
@@ -190,6 +199,8 @@ pipe_kernel(const JobPtrs *__restrict__ jobs, int njobs, float2 *psi1, const ROp
   const uint32_t a_tiles = (uint32_t)__cvta_generic_to_shared(tiles);
   const uint32_t a_full = (uint32_t)__cvta_generic_to_shared(s_full);
   const uint32_t a_done = (uint32_t)__cvta_generic_to_shared(s_done);
+  const uint32_t a_jobs = (uint32_t)__cvta_generic_to_shared(s_job);
+  const uint32_t a_ops = (uint32_t)__cvta_generic_to_shared(s_op);
 
   // the pass's program, once for the whole sweep (one job: its ops too)
   {
@@ -216,7 +227,8 @@ pipe_kernel(const JobPtrs *__restrict__ jobs, int njobs, float2 *psi1, const ROp
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kPipeRegsProducer));
     const int pt = tid - 2 * NT;
     auto amps = [&](unsigned u) -> float2 * {
-      return BATCH ? static_cast<float2 *>(jobs[u >> lt].psi) : psi1;
+      return BATCH ? reinterpret_cast<float2 *>(reinterpret_cast<char *>(psi1) + (long long)(u >> lt) * jstride)
+                   : psi1;
     };
     bool ok = true;
     for (unsigned i = 0; i < nloc + 3u; ++i) {
@@ -233,6 +245,17 @@ pipe_kernel(const JobPtrs *__restrict__ jobs, int njobs, float2 *psi1, const ROp
       }
       if (i < nloc && !probe) {
         const unsigned u = blockIdx.x + i * G;
+        if (BATCH) {
+          // the unit's job pointers and ops beside its tile
+          const JobPtrs *src = jobs + (u >> lt);
+          if (pt < (int)(sizeof(JobPtrs) / 8))
+            sw2::cp_async8(a_jobs + (uint32_t)sizeof(JobPtrs) * b + 8u * pt, reinterpret_cast<const char *>(src) + 8 * pt);
+          const ROpRes *so =
+              reinterpret_cast<const ROpRes *>(reinterpret_cast<const char *>(sops1) + (long long)(u >> lt) * jstride) +
+              d.rop0;
+          const uint32_t ab = a_ops + 16u * (uint32_t)kPipeBatchOps * b;
+          for (int w = pt; w < d.nrops; w += NT) sw2::cp_async16(ab + 16u * w, so + w);
+        }
         sw2::load_tile<RB>(amps(u), sw2::tile_origin(u & (T - 1u), d, M), d, pt, LOGNT, a_tiles + 8u * TA * b);
         pipe::cp_async_arrive(a_full + 8u * b);
         // unit i + 1 into L2 while unit i - 2 computes: its gather at the
@@ -263,40 +286,35 @@ pipe_kernel(const JobPtrs *__restrict__ jobs, int njobs, float2 *psi1, const ROp
     }
     const unsigned u = blockIdx.x + i * G;
     const unsigned tile = u & (T - 1u);
-    const JobPtrs jp = jobs[BATCH ? (u >> lt) : 0u];
-    const ROpRes *ops = BATCH ? jp.sops + d.rop0 : s_op;
+    // the unit's job pointers: BATCH from its buffer's slot, which stays
+    // valid until the buffer is handed back
+    const JobPtrs *js = BATCH ? &s_job[b] : jobs;
+    const ROpRes *ops = BATCH ? s_op + kPipeBatchOps * b : s_op;
     const uint64_t base = sw2::tile_origin(tile, d, M);
     float up = 0.f, dn = 0.f;
-    sw2::run_phases<RB, false, false>(tiles + b * TA, d, s_ph, ops, base, gt, LOGNT, M, jp.qdiag, up, dn, sH[g],
+    sw2::run_phases<RB, false, false>(tiles + b * TA, d, s_ph, ops, base, gt, LOGNT, M, js->qdiag, up, dn, sH[g],
                                       sQ[g], &sOut[g], nullptr, sync);
     // run_phases ends with the group's barrier: the tile is finished
-    if (gt == 0) pipe::mbar_arrive(a_done + 8u * b);
-    if (d.has_reduce) {
-      // the tile's partial, summed as reduce_finalize sums a block's
-      double pu = (double)up, pv = (double)dn;
-      for (int o = 16; o; o >>= 1) {
-        pu += __shfl_xor_sync(0xffffffffu, pu, o);
-        pv += __shfl_xor_sync(0xffffffffu, pv, o);
-      }
-      if ((gt & 31) == 0) s_up[g][gt >> 5] = pu, s_dn[g][gt >> 5] = pv;
-      sync();
-      if (gt == 0) {
-        double U = 0.0, D = 0.0;
-        for (int w = 0; w < NW; ++w) U += s_up[g][w], D += s_dn[g][w];
-        jp.partials[tile] = make_double2(U, D);
-        if (BATCH) {
-          // the job's last tile of this sweep combines its partials
-          __threadfence();
-          s_last[g] = (atomicAdd(jp.ticket, 1u) == T - 1u);
-        }
-      }
-      if (BATCH) {
-        sync();
-        if (s_last[g] && !probe) {
-          __threadfence();
-          pipe_finalize<NW>(jp, T, gt, err, s_up[g], s_dn[g], sync);
-        }
-      }
+    if (!d.has_reduce) {
+      if (gt == 0) pipe::mbar_arrive(a_done + 8u * b);
+      continue;
+    }
+    // the tile's partial, summed as reduce_finalize sums a block's; the
+    // buffer goes back after the group's barrier below, once every thread
+    // has read the job's reduction pointers from its slot
+    double2 *const partials = js->partials;
+    double pu = (double)up, pv = (double)dn;
+    for (int o = 16; o; o >>= 1) {
+      pu += __shfl_xor_sync(0xffffffffu, pu, o);
+      pv += __shfl_xor_sync(0xffffffffu, pv, o);
+    }
+    if ((gt & 31) == 0) s_up[g][gt >> 5] = pu, s_dn[g][gt >> 5] = pv;
+    sync();
+    if (gt == 0) {
+      pipe::mbar_arrive(a_done + 8u * b);
+      double U = 0.0, D = 0.0;
+      for (int w = 0; w < NW; ++w) U += s_up[g][w], D += s_dn[g][w];
+      partials[tile] = make_double2(U, D);
     }
   }
   if (BATCH || !d.has_reduce || probe) return;
@@ -307,12 +325,23 @@ pipe_kernel(const JobPtrs *__restrict__ jobs, int njobs, float2 *psi1, const ROp
   // one job: the last block to finish combines the tile partials (group 0)
   if (tid == 0) {
     const unsigned t = atomicAdd(jobs[0].ticket, 1u);
-    s_last[0] = (t == G - 1u);
+    s_last = (t == G - 1u);
   }
   both();
-  if (!s_last[0] || tid >= NT) return;
+  if (!s_last || tid >= NT) return;
   __threadfence();
-  pipe_finalize<NW>(jobs[0], T, tid, err, s_up[0], s_dn[0], sync);
+  const JobPtrs j0 = jobs[0];
+  pipe_finalize<NW>(j0.partials, j0.ticket, j0.step, j0.series, T, tid, err, s_up[0], s_dn[0], sync);
+}
+
+// After a batch's reducing pipelined sweep: block j sums job j's T tile
+// partials (128 threads, the order of reduce_finalize) and appends its (P,
+// norm), NaN when err is set.
+__global__ void __launch_bounds__(128) pipe_finalize_kernel(const JobPtrs *__restrict__ jobs, unsigned T,
+                                                            const int *err) {
+  __shared__ double su[4], sd[4];
+  const JobPtrs jp = jobs[blockIdx.x];
+  pipe_finalize<4>(jp.partials, jp.ticket, jp.step, jp.series, T, threadIdx.x, err, su, sd, sw2::SyncBlock{});
 }
 
 }  // namespace spinrp
