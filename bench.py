@@ -296,7 +296,9 @@ def run_batch(args, rank: int, world: int, local_rank: int):
                       "parallelism": "replicas" if world > 1 else "single GPU"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                        "kernel": "sweep2_kernel + resident_kernel (all sweep launches of the batch)",
+                        "kernel": ("pipe_kernel + sweep2_kernel + resident_kernel" if b.pipeline_groups()
+                                   else "sweep2_kernel + resident_kernel") + " (all sweep launches of the batch)",
+                        "pipelined_groups": b.pipeline_groups(),
                         "algorithmic_bytes": "one read and one write of every state per planned sweep "
                                              "(once per evolve call for states resident in shared memory)",
                         "algorithmic_bytes_per_batch_job": plan_bytes,
