@@ -1472,7 +1472,8 @@ static int launch_pass(const LaunchCtx &c, int pass, cudaStream_t stream, bool l
     const unsigned ahead = c.prefetch_ahead;
     const ROpRes *sops1 = c.njobs == 1 ? c.job0.sops : nullptr;
     const int code = (c.rb == 6 ? 4 : 0) | (sites ? 2 : 0) | (c.oriented ? 1 : 0);
-    if (c.pipe_blocks && code == 4 && K == 13) {
+    const bool piped = c.pipe_blocks && K == 13 && code == 4;
+    if (piped) {
       if (c.njobs == 1)
         pipe_kernel<6, 13, false><<<c.pipe_blocks, kPipeThreads, kPipeSmem, stream>>>(
             c.jobs, 1, psi1, sops1, 0, pd, c.phases, c.M, c.pipe_err, 0);
@@ -1487,23 +1488,21 @@ static int launch_pass(const LaunchCtx &c, int pass, cudaStream_t stream, bool l
           pipe_finalize_kernel<<<c.njobs, 128, 0, stream>>>(c.jobs, 1u << (c.M - 13), c.pipe_err);
         }
       }
-      CUDA_TRY(cudaGetLastError());
-      if (live && c.prof) prof_mark(c.prof, SPINRP_KERNEL_SWEEP);
-      return SPINRP_OK;
-    }
+    } else {
 #define SW2(RB_, S_, O_) \
   sweep2_kernel<RB_, S_, O_><<<grid, 1 << (K - RB_), sm2, stream>>>(c.jobs, psi1, sops1, pd, c.phases, c.M, ahead)
-    switch (code) {
-      case 0: SW2(5, false, false); break;
-      case 1: SW2(5, false, true); break;
-      case 2: SW2(5, true, false); break;
-      case 3: SW2(5, true, true); break;
-      case 4: SW2(6, false, false); break;
-      case 5: SW2(6, false, true); break;
-      case 6: SW2(6, true, false); break;
-      default: SW2(6, true, true); break;
-    }
+      switch (code) {
+        case 0: SW2(5, false, false); break;
+        case 1: SW2(5, false, true); break;
+        case 2: SW2(5, true, false); break;
+        case 3: SW2(5, true, true); break;
+        case 4: SW2(6, false, false); break;
+        case 5: SW2(6, false, true); break;
+        case 6: SW2(6, true, false); break;
+        default: SW2(6, true, true); break;
+      }
 #undef SW2
+    }
   }
   else if (sizeof(R) == 8 && c.v2 && !sites)
     // complex128 register-blocked (the all-site sums run in the plain kernel)

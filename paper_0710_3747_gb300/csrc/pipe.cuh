@@ -150,7 +150,9 @@ __device__ __forceinline__ void pipe_finalize(const double2 *partials, unsigned 
 }
 
 // One sweep (complex64, plain storage, spin-1 readout) with 2^(K-RB) = 128
-// threads per compute group.
+// threads per compute group.  (A sweep that takes the all-site readout runs
+// sweep2_kernel's readout variant: under this kernel's 224-register budget
+// the readout's sums spill, measured 8 % slower per step at M = 30.)
 //   BATCH = false: one job; jobs[0] holds its pointers (gate tables,
 //     partials, ticket, series), psi1 and sops1 its amplitudes and resolved
 //     ops; the units are its tiles, and the last block to finish combines

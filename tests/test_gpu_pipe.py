@@ -195,3 +195,29 @@ def test_pipeline_waits_are_bounded():
     small = _state(W.ladder(10, 1.0, 0.5), spinrp.XY, None, 1, True)
     rc, _ = small.pipeline_timeout_check()
     assert rc == spinrp.ESTATE
+
+
+@pytest.mark.parametrize("kind,M", [("ladder", 24), ("xy_ising_ladder", 24)])
+def test_pipelined_all_site_readout(kind, M):
+    """All-site readout (P of every spin after every step) from the pipelined
+    sweep: against the oracle's all-site series, and bit for bit against the
+    one-tile-per-block readout (every site's series and the raw buffer)."""
+    J, ht, a = _system(kind, M)
+    seed, dt, steps = 17, 0.05, 6
+    Pw, _, _ = oracle.run_all_sites(J, ht, seed, dt, steps, a_generic=a, threads=THREADS)
+    out = {}
+    for pipe in (True, False):
+        st = _state(J, ht, a, steps, pipe).set_sites(True)
+        assert st.pipeline() == pipe
+        st.init_random_phase(seed)
+        st.evolve(dt, 2).evolve(dt, 4)
+        out[pipe] = (st.site_series(), st.polarization(1), _raw(st))
+        st.close()
+    got = out[True][0]
+    assert got.shape == (steps + 1, M)
+    assert np.max(np.abs(got - Pw)) <= 1e-5
+    import torch
+
+    assert np.array_equal(out[True][0], out[False][0])
+    assert np.array_equal(out[True][1], out[False][1])
+    assert torch.equal(out[True][2], out[False][2])
