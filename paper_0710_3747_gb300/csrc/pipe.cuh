@@ -20,8 +20,9 @@
 // 224, what the phases need without spilling): 128 x 56 + 256 x 224 = 64512.
 //
 // Three tile buffers rotate through load -> phases -> store.  Block b takes
-// the tiles b, b + G, b + 2G, ... (G blocks), local tile i in buffer i mod 3
-// and in group i mod 2; shared-memory mbarriers hand a buffer over: full[k]
+// the units b, b + G, b + 2G, ... (G blocks; a unit is a tile, or for a batch
+// one job's tile), local unit i in buffer i mod 3 and in group i mod 2;
+// shared-memory mbarriers hand a buffer over: full[k]
 // completes when the producer's copies of the tile in buffer k have landed
 // (cp.async arrive-on), done[k] when a group has finished its phases on it.
 // While the groups compute two tiles, the producer writes back the previous
@@ -29,8 +30,9 @@
 //
 // Every amplitude goes through the same floating-point operations in the
 // same order as in sweep2_kernel, each tile's (N_up, N_dn) partial is summed
-// the same way, and the partials are combined in tile order by one group the
-// way reduce_finalize combines block partials: the results are the same bit
+// the same way, and a job's partials are combined in tile order the way
+// reduce_finalize combines block partials (one job: by the last block to
+// finish; a batch: by pipe_finalize_kernel): the results are the same bit
 // for bit.
 //
 // Waits are bounded by the global timer (kPipeWaitNs).  A wait that runs out
