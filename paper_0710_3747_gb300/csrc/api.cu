@@ -303,10 +303,12 @@ extern "C" int spinrp_system_set_regbits(spinrp_system *sys, int rb) {
 // SM) a sweep costs kPipeSweepCost of the model's sweep: measured per-sweep
 // time of the pipelined 13-spin sweep over the 14-spin one 0.58, 0.59 and
 // 0.72 on dipolar stars of 23, 24 and 26 spins, 0.48, 0.70 and 0.67 on
-// ladders of 24, 26 and 28 spins (K = 13 then the fastest width for all six
-// but the 24-spin ladder, 4 % slower than K = 14 there).
+// ladders of 24, 26 and 28 spins, 0.49 and 0.47 on batches of 383 and 363
+// dipolar stars of 20 and 21 spins (8 sweeps per step against 4: 29.2
+// against 30.0 and 57.8 against 62.2 ms per step); with 0.5 the model picks
+// 13, the fastest width, in all eight cases.
 constexpr int kModelSMs = 152;  // SMs of the GB300 the model was measured on
-constexpr double kPipeSweepCost = 0.6;
+constexpr double kPipeSweepCost = 0.5;
 static int make_plan(const spinrp_system &s, int prec, Plan *plan, int njobs = 1) {
   std::string err;
   const int c = low_bits(prec);

@@ -155,7 +155,7 @@ def test_plan_sweep_counts():
 def test_default_tile_model():
     """Default complex64 tile width: sweeps per step x max(2^K, 2^M / 152),
     least cost among 14, 13, 12 spins, ties to 13 then 12 (values from the
-    plan's own sweep counts), the 13-spin cost weighted by 0.6 where that plan
+    plan's own sweep counts), the 13-spin cost weighted by 0.5 where that plan
     runs as the pipelined sweep (at least 4 x 152 tiles: M >= 23); complex128:
     the widest K <= 12 leaving at least 128 tiles, at least 8."""
     def pick(J, ht):
@@ -170,11 +170,11 @@ def test_default_tile_model():
             s.set_tile("c64", K)
             costs[K] = s.plan_info("c64")["sweeps_per_step"] * max(2.0 ** K, 2.0 ** M / 152)
             if K == 13 and 2.0 ** (M - 13) >= 4 * 152:
-                costs[K] *= 0.6
+                costs[K] *= 0.5
         best = min(costs.values())
         return next(K for K in (13, 12, 14) if K in costs and costs[K] == best)
     cases = [(W.ladder(5), spinrp.XY, 10), (W.ladder(7), spinrp.XY, 12), (W.ladder(9), spinrp.XY, 12),
-             (W.ladder(11), spinrp.XY, 13), (W.ladder(12), spinrp.XY, 14), (W.ladder(15), spinrp.XY, 13),
+             (W.ladder(11), spinrp.XY, 13), (W.ladder(12), spinrp.XY, 13), (W.ladder(15), spinrp.XY, 13),
              (W.star_dipolar(16, 3), spinrp.DIPOLAR, 12), (W.star_dipolar(20, 2), spinrp.DIPOLAR, 12),
              (W.star_dipolar(22, 3), spinrp.DIPOLAR, 13), (W.star_dipolar(23, 3), spinrp.DIPOLAR, 13),
              (W.star_dipolar(24, 3), spinrp.DIPOLAR, 13), (W.star_dipolar(26, 3), spinrp.DIPOLAR, 13),
