@@ -186,6 +186,27 @@ def test_default_tile_model():
         assert s.plan_info("c128")["K"] == next((K for K in range(12, 7, -1) if M - K >= 7), min(8, M))
 
 
+def test_tile_model_weights_only_pipelined_plans():
+    """The 0.5 weight applies only where the 13-spin plan runs as the
+    pipelined sweep: six register bits and enough tiles.  With five register
+    bits forced, a 24-spin star and the 2x12 ladder go back to 14-spin tiles
+    (fewer sweeps per step); a 22-spin star (512 tiles, fewer than 4 x 152)
+    is not weighted either."""
+    for J, ht, sweeps13 in ((W.star_dipolar(24, 3), spinrp.DIPOLAR, 12), (W.ladder(12), spinrp.XY, 4)):
+        s = spinrp.System(J, ht)
+        assert s.plan_info("c64") == {"segments": (sweeps13 + 2) // 2, "sweeps_per_step": sweeps13, "K": 13}
+        s.set_regbits(5)
+        assert s.plan_info("c64")["K"] == 14
+    s = spinrp.System(W.star_dipolar(22, 3), spinrp.DIPOLAR)
+    costs = {}
+    for K in (13, 12, 14):
+        t = spinrp.System(W.star_dipolar(22, 3), spinrp.DIPOLAR)
+        t.set_tile("c64", K)
+        costs[K] = t.plan_info("c64")["sweeps_per_step"] * max(2.0 ** K, 2.0 ** 22 / 152)
+    best = min(costs.values())
+    assert s.plan_info("c64")["K"] == next(K for K in (13, 12, 14) if costs[K] == best)
+
+
 def test_plan_cache_keys():
     """Plans are cached by bond list, S^zS^z presence, precision and tile /
     register settings: systems with equal keys share a plan (schedule and
