@@ -78,13 +78,16 @@ def _priority(job: W.Job) -> int:
     return -2 if w < 1e10 else (-1 if w < 1e12 else 0)
 
 
-def _start(job: W.Job, prec: str, now: float, tile_K: int | None, priority: int = 0) -> _Active:
+def _start(job: W.Job, prec: str, now: float, tile_K: int | None, priority: int = 0,
+           pipeline: bool = True) -> _Active:
     import torch
     stream = torch.cuda.Stream(priority=priority)
     sysm = spinrp.System(job.J, job.htype)
     if tile_K:
         sysm.set_tile(prec, min(tile_K, job.M))
     st = spinrp.State(sysm, prec, series_cap=job.steps + 1, stream=stream.cuda_stream)
+    if not pipeline:
+        st.set_pipeline(False)
     st.init_random_phase(job.seed)
     p, w = st.psi_bytes, st.work_bytes
     res = Result(job.meta.get("index", -1), job.M, job.kind, job.steps, job.arrival, start=now)
@@ -114,7 +117,7 @@ def run_stream(jobs: list[W.Job], prec: str = "c64", max_active: int = 16,
                hbm_budget: int | None = None, chunk: int = 20, tile_K: int | None = None,
                realtime: bool = True, start_fn=None, finish_fn=None, footprint_fn=None,
                trace: list | None = None, depth: int = 2, priorities: bool = True,
-               policy: str = "fifo") -> list[Result]:
+               policy: str = "fifo", pipeline: bool = True) -> list[Result]:
     """Serve `jobs` (sorted by arrival) with continuous batching.
 
     realtime: arrivals follow the wall clock (t = 0 at the call); otherwise all
@@ -126,7 +129,9 @@ def run_stream(jobs: list[W.Job], prec: str = "c64", max_active: int = 16,
     memory and slot freed) as soon as its last chunk has finished.  Each job's
     footprint is computed once.  policy "fifo" admits arrived jobs in arrival
     order; "sjf" admits, among the arrived jobs, the one with the least work
-    (amplitude-gate updates) first.  start_fn / finish_fn / footprint_fn replace
+    (amplitude-gate updates) first.  pipeline False keeps every job's sweeps
+    one tile per block (a pipelined sweep holds every SM for its duration,
+    so the other jobs' blocks wait for it).  start_fn / finish_fn / footprint_fn replace
     the device calls (host-side tests); `trace`, when given, receives
     ("admit" | "chunk" | "done", job index, bytes in use)."""
     footprint_fn = footprint_fn or footprint
@@ -173,7 +178,7 @@ def run_stream(jobs: list[W.Job], prec: str = "c64", max_active: int = 16,
             if used + need[k] > hbm_budget:
                 break
             if start_fn is _start:
-                a = _start(j, prec, now(), tile_K, _priority(j) if priorities else 0)
+                a = _start(j, prec, now(), tile_K, _priority(j) if priorities else 0, pipeline)
             else:
                 a = start_fn(j, prec, now(), tile_K)
             active.append(a)
@@ -220,7 +225,7 @@ def run_stream(jobs: list[W.Job], prec: str = "c64", max_active: int = 16,
 
 
 def run_sequential(jobs: list[W.Job], prec: str = "c64", tile_K: int | None = None,
-                   realtime: bool = True, chunk: int | None = None) -> list[Result]:
+                   realtime: bool = True, chunk: int | None = None, pipeline: bool = True) -> list[Result]:
     """The same jobs one at a time, each started when it has arrived and the
     previous one is done (in evolve calls of `chunk` steps when given, else
     one call per job)."""
@@ -231,7 +236,7 @@ def run_sequential(jobs: list[W.Job], prec: str = "c64", tile_K: int | None = No
     for j in sorted(jobs, key=lambda j: j.arrival):
         if realtime and j.arrival > now():
             time.sleep(j.arrival - now())
-        a = _start(j, prec, now(), tile_K)
+        a = _start(j, prec, now(), tile_K, pipeline=pipeline)
         left = j.steps
         while left > 0:
             n = left if not chunk else min(chunk, left)
@@ -264,6 +269,8 @@ def main(argv=None):
     ap.add_argument("--no-priorities", action="store_true", help="all job streams at the default priority")
     ap.add_argument("--policy", choices=["fifo", "sjf"], default="fifo",
                     help="admission order among arrived jobs: arrival, or least work first")
+    ap.add_argument("--no-pipeline", action="store_true",
+                    help="every job's sweeps one tile per block (no pipelined sweeps)")
     ap.add_argument("--mode", choices=["both", "continuous", "sequential"], default="both",
                     help="which modes to run (one per process keeps each run's device state apart)")
     args = ap.parse_args(argv)
@@ -284,7 +291,8 @@ def main(argv=None):
     work = sum(job_work(j) for j in jobs)
     Ms = [j.M for j in jobs]
     out = {"jobs": len(jobs), "saturated": args.saturated, "rate_per_s": None if args.saturated else rate,
-           "M_range": [min(Ms), max(Ms)], "amp_gate_updates": work, "policy": args.policy}
+           "M_range": [min(Ms), max(Ms)], "amp_gate_updates": work, "policy": args.policy,
+           "pipelined_sweeps": not args.no_pipeline}
     res = {}
     for mode in ("continuous", "sequential"):
         if args.mode not in ("both", mode):
@@ -292,9 +300,10 @@ def main(argv=None):
         t = time.perf_counter()
         if mode == "continuous":
             r = run_stream(jobs, args.prec, max_active=args.max_active, chunk=args.chunk, tile_K=tile_K,
-                           realtime=realtime, priorities=not args.no_priorities, policy=args.policy)
+                           realtime=realtime, priorities=not args.no_priorities, policy=args.policy,
+                           pipeline=not args.no_pipeline)
         else:
-            r = run_sequential(jobs, args.prec, tile_K=tile_K, realtime=realtime)
+            r = run_sequential(jobs, args.prec, tile_K=tile_K, realtime=realtime, pipeline=not args.no_pipeline)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t
         res[mode] = r
