@@ -307,13 +307,14 @@ int spinrp_state_layout(const spinrp_state *st, int32_t *layout, void **psi);
  * state stored plainly.  Host only. */
 int spinrp_state_orientation(const spinrp_state *st, uint64_t *black);
 
-/* Pipelined sweeps (no counterpart in the paper; the same Trotter steps of
- * Sec. 3, Eq. 3, scheduled differently).  A complex64 state whose plan uses
- * 13-spin tiles and six register bits, plainly stored, with at least four
- * tiles per SM (M >= 23 on GB300), runs each sweep as one persistent launch
- * of one block per SM: a producer warp gathers tiles into three shared-memory
- * buffers and writes them back while two compute groups apply the sweep's
- * gates, so the state's streaming through HBM overlaps the arithmetic.
+/* Pipelined sweeps (no counterpart in the paper; the same second-order
+ * Trotter-Suzuki steps, the product the introduction and summary name,
+ * scheduled differently).  A complex64 state whose plan uses 13-spin tiles
+ * and six register bits, plainly stored, with at least four tiles per SM
+ * (M >= 23 on GB300), runs each sweep as one persistent launch of one block
+ * per SM: a producer warpgroup gathers tiles into three shared-memory buffers
+ * and writes them back while two compute warpgroups apply the sweep's gates,
+ * so the state's streaming through HBM overlaps the arithmetic.
  * on = 1 (the default) uses it where the plan takes it, on = 0 the
  * one-tile-per-block sweep; the amplitudes and series are the same bit for
  * bit.  Takes effect at the next evolve.  Host only.  Errors: SPINRP_EINVAL.
